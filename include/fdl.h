@@ -1,0 +1,187 @@
+/*
+ * fdl.h -- C ABI of the GB300 (sm_103a) Fourier Disparity Layer library.
+ *
+ * The operations follow Le Pendu, Guillemot, Smolic, "A Fourier Disparity
+ * Layer representation for Light Fields" (arXiv 1901.06919):
+ *   - layer construction (Sec. V-A): a 2D DFT of every input view, then at
+ *     every spatial frequency w the Tikhonov least-squares solve
+ *     (A*A + lambda Gamma*Gamma) x = A* b, A_jk = exp(+2 pi i d_k (u_j . w))
+ *     (Eqs. AMatGeneral, LayerConstructProb, LayerConstructionClosedForm);
+ *   - rendering (Sec. VI-A): the layer spectra phase-shifted, aperture
+ *     filtered and summed (Eq. BsFourier), then an inverse DFT;
+ *   - calibration (Sec. V-B): the objective of Eq. CalibrationProb and its
+ *     gradient with respect to view positions and disparities (Eqs. gradP,
+ *     gradD).
+ *
+ * Conventions used by every entry point.
+ *   Memory: every array argument is a DEVICE pointer unless it says "host".
+ *     All memory is owned by the caller; the library allocates nothing and
+ *     keeps no state between calls.  Scratch memory is a caller workspace
+ *     whose size comes from the matching *_workspace_size() query; the
+ *     workspace must be 256-byte aligned.
+ *   Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *     only enqueue work; they do not synchronise, except where stated.
+ *   Complex numbers: interleaved float pairs (re, im), i.e. complex64.
+ *   Images: float32 [C][H][W] row-major (y = row); H and W powers of two,
+ *     16 <= H, W <= 4096.
+ *   Spectra: the non-negative-kx half of the 2D DFT, complex64
+ *     [..][H][W/2+1] (the layout of torch.fft.rfft2).  Frequencies are in
+ *     cycles per pixel: w_y = ky/H for ky < H/2, (ky-H)/H otherwise;
+ *     w_x = kx/W for kx = 0..W/2.  The forward DFT is unnormalised with
+ *     sign -: b(w) = sum_x B(x) exp(-2 pi i w.x).
+ *   Views: u is float32 [K][2] = (u_x, u_y) per view in view-grid units;
+ *     a layer of disparity d is seen from u as layer(x + u d) (Appendix A,
+ *     Eq. Prior2).  Disparities d are float32 [N], pixels per unit of u.
+ *   Errors: every call returns FDL_OK or a positive FDL_E* code and never
+ *     aborts; fdl_strerror() names a code.  Invalid arguments are rejected
+ *     before anything is enqueued.
+ */
+#ifndef FDL_H
+#define FDL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FDL_API __attribute__((visibility("default")))
+#else
+#define FDL_API
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FDL_OK 0
+#define FDL_EINVAL 1   /* bad shape, count, pointer or option              */
+#define FDL_ENOMEM 2   /* workspace smaller than the *_workspace_size()    */
+#define FDL_ECUDA 3    /* a kernel launch or CUDA runtime call failed       */
+#define FDL_ETIMEOUT 4 /* a bounded wait ran out                            */
+#define FDL_ENOTSUP 5  /* valid request this build does not support         */
+
+/* ---- regularisers, Sec. V-C -------------------------------------------- */
+#define FDL_REG_VIEW2 0  /* Gamma*Gamma = diag(|w|^4 d_k^4 + eps), Eq. 2ndOrderView */
+#define FDL_REG_LAYER2 1 /* Gamma = tridiag(1,-2,1), Eq. 2ndOrderLayer              */
+#define FDL_REG_L2 2     /* Gamma = I (Sec. V-C)                                     */
+
+/* ---- arithmetic of the per-frequency solve ----------------------------- */
+#define FDL_PREC_MIXED 0 /* FP32 where the estimated condition number of
+                            A*A + lambda Gamma*Gamma is below kappa_max;
+                            double-float (FP32 pairs, ~2^-48) elsewhere     */
+#define FDL_PREC_DF 1    /* double-float at every frequency                   */
+#define FDL_PREC_F64 2   /* native FP64 at every frequency                    */
+#define FDL_PREC_F32 3   /* FP32 at every frequency, no certification         */
+
+/* ---- apertures psi of Eq. refocus, normalised to integrate to 1 ------- */
+#define FDL_AP_PINHOLE 0 /* psi = delta: psi_hat = 1 (sub-aperture image)    */
+#define FDL_AP_DISC 1    /* disc of radius r: 2 J1(2 pi r|v|) / (2 pi r|v|)    */
+#define FDL_AP_SQUARE 2  /* square of half side r: sinc(2 r v_x) sinc(2 r v_y) */
+#define FDL_AP_POINTS 3  /* (1/M) sum_m delta(u - u_m): discrete aperture     */
+
+typedef struct fdl_fit_opts {
+  double lambda;    /* Tikhonov weight lambda of Eq. LayerConstructProb, >= 0      */
+  double eps;       /* epsilon added to the view regulariser's diagonal (Sec. V-C1;
+                       the diagonal is lambda (|w|^4 d^4 + eps)); unused otherwise */
+  int reg;          /* FDL_REG_*                                                   */
+  int precision;    /* FDL_PREC_*                                                  */
+  double kappa_max; /* FDL_PREC_MIXED: largest estimated condition number kept in
+                       FP32 (<= 0 selects the default, 100)                        */
+} fdl_fit_opts;
+
+/* One image to render (Eq. BsFourier): the FDL it reads, the viewpoint u0,
+ * the focus disparity s and the aperture. */
+typedef struct fdl_request {
+  const float* layers; /* device complex64 [N][C][H][W/2+1]                     */
+  const float* d;      /* device float32 [N]                                    */
+  float* out;          /* device float32 [C][H][W]                              */
+  const float* pts;    /* FDL_AP_POINTS: device float32 [npts][2] offsets u_m   */
+  int N, npts;
+  int aperture;        /* FDL_AP_*                                              */
+  float u0x, u0y;      /* viewpoint on the camera plane                         */
+  float s;             /* refocus parameter (disparity in focus), Sec. III      */
+  float radius;        /* disc radius / square half side, in units of u (the
+                          aperture-size factor f of Sec. VI-A)                  */
+  int pad_;            /* keeps the struct a multiple of 8 bytes; set to 0      */
+} fdl_request;
+
+FDL_API const char* fdl_strerror(int status);
+FDL_API int fdl_version(void);
+
+/* ---- 2D real DFTs (Sec. V-A: "discrete Fourier Transform of each image";
+ *      Sec. VI-A: inverse transform; Sec. VII: half spectrum) ------------ */
+
+/* spectra[i] = half spectrum of image i, for nimg images [nimg][H][W]. */
+FDL_API size_t fdl_rfft2_workspace_size(int nimg, int H, int W);
+FDL_API int fdl_rfft2(const float* images, int nimg, int H, int W, float* spectra,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* images[i] = Re(inverse DFT of spectrum i completed by X(-w) = conj X(w)) / (H W),
+ * i.e. the kx = 0 and kx = W/2 columns count through their Hermitian part. */
+FDL_API size_t fdl_irfft2_workspace_size(int nimg, int H, int W);
+FDL_API int fdl_irfft2(const float* spectra, int nimg, int H, int W, float* images,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- layer construction (Sec. V-A) ------------------------------------ */
+
+/* views [K][C][H][W] float32, u [K][2], d [N]  ->  layers [N][C][H][W/2+1]
+ * complex64.  1 <= N <= 64, 1 <= K <= 1024, 1 <= C <= 4.  The channels share A and Gamma: one factorisation per
+ * frequency serves all C right-hand sides.  The spectra of the views are
+ * kept in the workspace. */
+FDL_API size_t fdl_fit_workspace_size(int K, int C, int H, int W, int N);
+FDL_API int fdl_fit(const float* views, int K, int C, int H, int W, const float* u,
+                    const float* d, int N, const fdl_fit_opts* opts, float* layers,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* Same solve from precomputed half spectra [K][C][H][W/2+1] complex64. */
+FDL_API size_t fdl_fit_spectra_workspace_size(int K, int C, int H, int W, int N);
+FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W,
+                            const float* u, const float* d, int N, const fdl_fit_opts* opts,
+                            float* layers, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* After fdl_fit / fdl_fit_spectra on `stream`: counts[0] = frequencies solved
+ * in FP32, counts[1] = frequencies solved in double-float or FP64, counts[2]
+ * = frequencies whose high-precision factorisation broke down (left as
+ * zeros), counts[3] = frequencies with non-finite input.  counts is a HOST
+ * int[4]; this call synchronises `stream`. */
+FDL_API int fdl_fit_tier_counts(const void* workspace, int* counts, void* stream);
+
+/* ---- rendering (Sec. VI-A, Eq. FourierView / Eq. BsFourier) ----------- */
+
+/* B sub-aperture views of one FDL at viewpoints u0 [B][2] (psi = delta):
+ * out [B][C][H][W]. */
+FDL_API size_t fdl_render_workspace_size(int B, int C, int H, int W);
+FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H, int W,
+                       const float* u0, int B, float* out, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
+/* B general images, each described by a request (req: DEVICE array [B]).
+ * The requests may read different FDLs, but all share H, W, C (the caller
+ * groups requests by image size).  If count is not NULL it is a DEVICE int:
+ * only requests [0, *count) are rendered, so that a captured CUDA graph can
+ * be replayed with a varying batch.  Every N must be <= Nmax <= 64. */
+FDL_API size_t fdl_refocus_workspace_size(int B, int C, int H, int W);
+FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, int H,
+                        int W, int Nmax, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
+/* ---- calibration (Sec. V-B) ------------------------------------------- */
+
+/* Over the frequencies listed in bins (DEVICE int [nbins], flattened index
+ * ky*(W/2+1)+kx of the stored half; NULL = every stored frequency), with the
+ * layers x re-solved at the current u, d by the closed form:
+ *   loss   = sum_{bins, c} |A x - b|^2 + lambda |Gamma x|^2 (Eq. CalibrationProb)
+ *   grad_u = dloss/du [K][2], grad_d = dloss/dd [N]      (Eqs. gradP, gradD)
+ * loss is a DEVICE float [1]; reg must be FDL_REG_LAYER2 or FDL_REG_L2
+ * (a regulariser that does not depend on d).  Arithmetic follows
+ * opts->precision as in fdl_fit. */
+FDL_API size_t fdl_calib_grad_workspace_size(int K, int C, int H, int W, int N, int nbins);
+FDL_API int fdl_calib_grad(const float* spectra, int K, int C, int H, int W, const float* u,
+                           const float* d, int N, const fdl_fit_opts* opts, const int* bins,
+                           int nbins, float* loss, float* grad_u, float* grad_d,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDL_H */

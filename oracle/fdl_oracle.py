@@ -81,6 +81,19 @@ def half_spectrum(img) -> np.ndarray:
     return dft2(img)[..., : W // 2 + 1]
 
 
+def dft_at_bins(img, ky, kx) -> np.ndarray:
+    """DFT of images ``[..., H, W]`` at listed bins by the definition (no FFT):
+    ``b = sum_{y,x} B(y, x) exp(-2 pi i (ky y / H + kx x / W))``; returns ``[..., nbins]``."""
+    img = np.asarray(img, np.float64)
+    H, W = img.shape[-2:]
+    ky = np.asarray(ky)
+    kx = np.asarray(kx)
+    ex = np.exp(-2j * np.pi * np.outer(np.arange(W), kx) / W)  # [W, nb]
+    ey = np.exp(-2j * np.pi * np.outer(np.arange(H), ky) / H)  # [H, nb]
+    rows = img @ ex  # [..., H, nb]
+    return np.einsum("...yb,yb->...b", rows, ey)
+
+
 def complete_half(S: np.ndarray, W: int) -> np.ndarray:
     """Full spectrum from a stored half: ``X(-w) := conj X(w)`` for ``kx > W/2``."""
     H = S.shape[-2]

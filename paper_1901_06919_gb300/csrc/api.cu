@@ -1,0 +1,334 @@
+// C ABI of libfdl: argument checks, workspace carving and kernel order.
+// Every function returns an FDL_* status and never throws or aborts.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "kernels.h"
+
+using namespace fdl;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+bool shape_ok(int H, int W) { return pow2_in(H, 16, 4096) && pow2_in(W, 16, 4096); }
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? FDL_OK : FDL_ECUDA; }
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* p) : base(static_cast<char*>(p)) {}
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+// Fit workspace: counters first (fdl_fit_tier_counts finds them there).
+struct FitWs {
+  int* counters;
+  float4* exp_table;
+  int* flagged;
+  float2* spec_main;
+  float2* spec_nyq;
+  size_t bytes;
+};
+
+FitWs carve_fit(void* ws, int K, int C, int H, int W, bool with_spectra) {
+  Carver cv(ws);
+  FitWs f;
+  f.counters = cv.take<int>(16);
+  f.exp_table = cv.take<float4>(1024);
+  f.flagged = cv.take<int>((size_t)H * (W / 2 + 1));
+  if (with_spectra) {
+    f.spec_main = cv.take<float2>((size_t)K * C * H * (W / 2));
+    f.spec_nyq = cv.take<float2>((size_t)K * C * H);
+  } else {
+    f.spec_main = f.spec_nyq = nullptr;
+  }
+  f.bytes = cv.off;
+  return f;
+}
+
+int check_fit_args(int K, int C, int H, int W, int N, const fdl_fit_opts* o) {
+  if (K < 1 || K > 1024 || C < 1 || C > 4 || N < 1 || N > 64 || !shape_ok(H, W)) return FDL_EINVAL;
+  if (!o) return FDL_EINVAL;
+  if (!(o->lambda >= 0.0) || !std::isfinite(o->lambda) || !(o->eps >= 0.0) || !std::isfinite(o->eps))
+    return FDL_EINVAL;
+  if (o->reg < FDL_REG_VIEW2 || o->reg > FDL_REG_L2) return FDL_EINVAL;
+  if (o->precision < FDL_PREC_MIXED || o->precision > FDL_PREC_F32) return FDL_EINVAL;
+  if (o->precision == FDL_PREC_F32 && N > 32) return FDL_ENOTSUP;
+  return FDL_OK;
+}
+
+int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const float* d, int N,
+              const fdl_fit_opts* o, float* layers, const FitWs& f, cudaStream_t st) {
+  SolveParams p;
+  p.b = b;
+  p.x = reinterpret_cast<float2*>(layers);
+  p.u = u;
+  p.d = d;
+  p.K = K;
+  p.C = C;
+  p.N = N;
+  p.H = H;
+  p.W = W;
+  p.reg = o->reg;
+  p.lam = (float)o->lambda;
+  p.lam_eps = (float)(o->lambda * (o->reg == FDL_REG_VIEW2 ? o->eps : 0.0));
+  p.lam_d = o->lambda;
+  p.lam_eps_d = o->lambda * (o->reg == FDL_REG_VIEW2 ? o->eps : 0.0);
+  p.kappa_max = (float)(o->kappa_max > 0.0 ? o->kappa_max : 100.0);
+  p.flagged = f.flagged;
+  p.counters = f.counters;
+  p.exp_table = f.exp_table;
+  cudaError_t e = cudaMemsetAsync(f.counters, 0, 16 * sizeof(int), st);
+  if (e != cudaSuccess) return FDL_ECUDA;
+  e = launch_exp_table(f.exp_table, st);
+  if (e != cudaSuccess) return FDL_ECUDA;
+  switch (o->precision) {
+    case FDL_PREC_F32:
+      e = launch_solve_f32(p, false, st);
+      break;
+    case FDL_PREC_DF:
+      e = launch_solve_hp(p, true, false, st);
+      break;
+    case FDL_PREC_F64:
+      e = launch_solve_hp(p, true, true, st);
+      break;
+    default:
+      if (N > 32) {
+        e = launch_solve_hp(p, true, false, st);
+      } else {
+        e = launch_solve_f32(p, true, st);
+        if (e == cudaSuccess) e = launch_solve_hp(p, false, false, st);
+      }
+  }
+  return cuda_status(e);
+}
+
+size_t spec_tmp_bytes(int nimg, int H, int W) { return align_up((size_t)nimg * H * (W / 2) * sizeof(float2)); }
+
+size_t render_ws_bytes(int B, int C, int H, int W, bool with_reqs) {
+  size_t s = 0;
+  if (with_reqs) s += align_up((size_t)B * sizeof(fdl_request));
+  s += align_up((size_t)B * C * H * (W / 2) * sizeof(float2));
+  s += align_up((size_t)B * C * H * sizeof(float2));
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+FDL_API const char* fdl_strerror(int status) {
+  switch (status) {
+    case FDL_OK:
+      return "ok";
+    case FDL_EINVAL:
+      return "invalid argument";
+    case FDL_ENOMEM:
+      return "workspace too small";
+    case FDL_ECUDA:
+      return "CUDA launch or runtime error";
+    case FDL_ETIMEOUT:
+      return "bounded wait timed out";
+    case FDL_ENOTSUP:
+      return "not supported by this build";
+    default:
+      return "unknown status";
+  }
+}
+
+FDL_API int fdl_version(void) { return 1; }
+
+// ------------------------------------------------------------------ DFTs
+FDL_API size_t fdl_rfft2_workspace_size(int nimg, int H, int W) {
+  if (nimg < 1 || !shape_ok(H, W)) return 0;
+  return spec_tmp_bytes(nimg, H, W);
+}
+
+FDL_API int fdl_rfft2(const float* images, int nimg, int H, int W, float* spectra, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  if (nimg < 1 || !shape_ok(H, W) || !images || !spectra || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_rfft2_workspace_size(nimg, H, W)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float2* tmp = static_cast<float2*>(workspace);
+  cudaError_t e = launch_rfft_rows(images, tmp, (long long)nimg * H, W, st);
+  if (e == cudaSuccess)
+    e = launch_fft_cols_fwd(spec_split(tmp, nullptr, H, W), spec_dense(reinterpret_cast<float2*>(spectra), H, W),
+                            nimg, H, W, st);
+  return cuda_status(e);
+}
+
+FDL_API size_t fdl_irfft2_workspace_size(int nimg, int H, int W) {
+  if (nimg < 1 || !shape_ok(H, W)) return 0;
+  return spec_tmp_bytes(nimg, H, W);
+}
+
+FDL_API int fdl_irfft2(const float* spectra, int nimg, int H, int W, float* images, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  if (nimg < 1 || !shape_ok(H, W) || !images || !spectra || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_irfft2_workspace_size(nimg, H, W)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float2* tmp = static_cast<float2*>(workspace);
+  cudaError_t e = launch_fft_cols_inv(spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W),
+                                      tmp, nimg, H, W, nullptr, 1, st);
+  if (e == cudaSuccess)
+    e = launch_irfft_rows(tmp, images, (long long)nimg * H, H, W, 1.f / ((float)H * (float)W), nullptr, nullptr, 1,
+                          st);
+  return cuda_status(e);
+}
+
+// ------------------------------------------------------------------ fit
+FDL_API size_t fdl_fit_workspace_size(int K, int C, int H, int W, int N) {
+  if (K < 1 || C < 1 || N < 1 || !shape_ok(H, W)) return 0;
+  return carve_fit(nullptr, K, C, H, W, true).bytes;
+}
+
+FDL_API int fdl_fit(const float* views, int K, int C, int H, int W, const float* u, const float* d, int N,
+                    const fdl_fit_opts* opts, float* layers, void* workspace, size_t workspace_bytes, void* stream) {
+  int s = check_fit_args(K, C, H, W, N, opts);
+  if (s != FDL_OK) return s;
+  if (!views || !u || !d || !layers || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_fit_workspace_size(K, C, H, W, N)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FitWs f = carve_fit(workspace, K, C, H, W, true);
+  const int nimg = K * C;
+  cudaError_t e = launch_rfft_rows(views, f.spec_main, (long long)nimg * H, W, st);
+  SpecView b = spec_split(f.spec_main, f.spec_nyq, H, W);
+  if (e == cudaSuccess) e = launch_fft_cols_fwd(b, b, nimg, H, W, st);
+  if (e != cudaSuccess) return FDL_ECUDA;
+  return run_solve(b, K, C, H, W, u, d, N, opts, layers, f, st);
+}
+
+FDL_API size_t fdl_fit_spectra_workspace_size(int K, int C, int H, int W, int N) {
+  if (K < 1 || C < 1 || N < 1 || !shape_ok(H, W)) return 0;
+  return carve_fit(nullptr, K, C, H, W, false).bytes;
+}
+
+FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W, const float* u, const float* d, int N,
+                            const fdl_fit_opts* opts, float* layers, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+  int s = check_fit_args(K, C, H, W, N, opts);
+  if (s != FDL_OK) return s;
+  if (!spectra || !u || !d || !layers || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_fit_spectra_workspace_size(K, C, H, W, N)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FitWs f = carve_fit(workspace, K, C, H, W, false);
+  SpecView b = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
+  return run_solve(b, K, C, H, W, u, d, N, opts, layers, f, st);
+}
+
+FDL_API int fdl_fit_tier_counts(const void* workspace, int* counts, void* stream) {
+  if (!workspace || !counts) return FDL_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int tmp[4];
+  cudaError_t e = cudaMemcpyAsync(tmp, workspace, sizeof(tmp), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return FDL_ECUDA;
+  std::memcpy(counts, tmp, sizeof(tmp));
+  return FDL_OK;
+}
+
+// ------------------------------------------------------------------ render
+FDL_API size_t fdl_render_workspace_size(int B, int C, int H, int W) {
+  if (B < 1 || C < 1 || C > 4 || !shape_ok(H, W)) return 0;
+  return render_ws_bytes(B, C, H, W, true);
+}
+
+FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H, int W, const float* u0, int B,
+                       float* out, void* workspace, size_t workspace_bytes, void* stream) {
+  if (B < 1 || C < 1 || C > 4 || N < 1 || N > 64 || !shape_ok(H, W)) return FDL_EINVAL;
+  if (!layers || !d || !u0 || !out || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_render_workspace_size(B, C, H, W)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(workspace);
+  fdl_request* req = cv.take<fdl_request>(B);
+  float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
+  float2* nyq = cv.take<float2>((size_t)B * C * H);
+  cudaError_t e = launch_pinhole_requests(req, layers, d, N, u0, B, out, (long long)C * H * W, st);
+  if (e == cudaSuccess) e = launch_render_spectra(req, B, nullptr, C, H, W, spec_split(main, nyq, H, W), st);
+  if (e == cudaSuccess) e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, nullptr, C, st);
+  if (e == cudaSuccess)
+    e = launch_irfft_rows(main, out, (long long)B * C * H, H, W, 1.f / ((float)H * (float)W), nullptr, nullptr, C, st);
+  return cuda_status(e);
+}
+
+FDL_API size_t fdl_refocus_workspace_size(int B, int C, int H, int W) {
+  if (B < 1 || C < 1 || C > 4 || !shape_ok(H, W)) return 0;
+  return render_ws_bytes(B, C, H, W, false);
+}
+
+FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  if (B < 1 || C < 1 || C > 4 || Nmax < 1 || Nmax > 64 || !shape_ok(H, W)) return FDL_EINVAL;
+  if (!req || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_refocus_workspace_size(B, C, H, W)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(workspace);
+  float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
+  float2* nyq = cv.take<float2>((size_t)B * C * H);
+  cudaError_t e = launch_render_spectra(req, B, count, C, H, W, spec_split(main, nyq, H, W), st);
+  if (e == cudaSuccess) e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, count, C, st);
+  if (e == cudaSuccess)
+    e = launch_irfft_rows(main, nullptr, (long long)B * C * H, H, W, 1.f / ((float)H * (float)W), req, count, C, st);
+  return cuda_status(e);
+}
+
+// ------------------------------------------------------------------ calibration
+FDL_API size_t fdl_calib_grad_workspace_size(int K, int C, int H, int W, int N, int nbins) {
+  (void)C;
+  (void)H;
+  (void)W;
+  (void)nbins;
+  if (K < 1 || N < 1) return 0;
+  return align_up(1024 * sizeof(float4)) + align_up((size_t)kCalibGrid * (1 + 2 * K + N) * sizeof(double));
+}
+
+FDL_API int fdl_calib_grad(const float* spectra, int K, int C, int H, int W, const float* u, const float* d, int N,
+                           const fdl_fit_opts* opts, const int* bins, int nbins, float* loss, float* grad_u,
+                           float* grad_d, void* workspace, size_t workspace_bytes, void* stream) {
+  int s = check_fit_args(K, C, H, W, N, opts);
+  if (s != FDL_OK && s != FDL_ENOTSUP) return s;
+  if (opts->reg == FDL_REG_VIEW2) return FDL_EINVAL;
+  if (!spectra || !u || !d || !loss || !grad_u || !grad_d || !workspace) return FDL_EINVAL;
+  if (bins && nbins < 1) return FDL_EINVAL;
+  if (workspace_bytes < fdl_calib_grad_workspace_size(K, C, H, W, N, nbins)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(workspace);
+  CalibParams p;
+  p.exp_table = cv.take<float4>(1024);
+  p.partials = cv.take<double>((size_t)kCalibGrid * (1 + 2 * K + N));
+  p.b = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
+  p.u = u;
+  p.d = d;
+  p.K = K;
+  p.C = C;
+  p.N = N;
+  p.H = H;
+  p.W = W;
+  p.reg = opts->reg;
+  p.lam = (float)opts->lambda;
+  p.lam_d = opts->lambda;
+  p.bins = bins;
+  p.nbins = bins ? nbins : 0;
+  p.loss = loss;
+  p.grad_u = grad_u;
+  p.grad_d = grad_d;
+  p.counters = nullptr;
+  p.f64 = opts->precision == FDL_PREC_F64;
+  cudaError_t e = launch_exp_table(const_cast<float4*>(p.exp_table), st);
+  if (e == cudaSuccess) e = launch_calib_grad(p, st);
+  return cuda_status(e);
+}
+
+}  // extern "C"

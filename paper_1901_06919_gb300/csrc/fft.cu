@@ -1,0 +1,399 @@
+// 2D real DFTs of the FDL path (Sec. V-A: the DFT of every input view;
+// Sec. VI-A: the inverse DFT of a rendered spectrum; Sec. VII: only the
+// non-negative-kx half is kept).
+//
+// Layout of a row-transformed image (the "split" layout): W/2 complex per row
+// (pitch W/2, so every row starts on a 16-byte boundary), element 0 packing
+// the two real values X[0] + i X[W/2]; after the column pass the kx = W/2
+// column lives in a separate [img][H] plane.
+//
+// Every FFT here is a Stockham autosort FFT (radix 4, one radix-2 pass when
+// log2 L is odd) run by a whole CTA on data staged in shared memory.
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace fdl {
+
+namespace {
+
+// tw[t] = exp(-2 pi i t / L)
+__device__ __forceinline__ void make_twiddles(float2* tw, int L) {
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    float s, c;
+    sincospif(-2.0f * (float)t / (float)L, &s, &c);
+    tw[t] = make_float2(c, s);
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 twid(const float2* tw, int i) {
+  float2 w = tw[i];
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+template <bool INV>
+__device__ __forceinline__ void radix4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = csub(a1, a3);
+  t3 = INV ? make_float2(-t3.y, t3.x) : make_float2(t3.y, -t3.x);  // times +i / -i
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+// In-place DFTs of `nfft` sequences of length L = 2^logL held in shared
+// memory at s[f * fstride + n * estride].  All threads of the CTA must call
+// it; each handles at most MAXB radix-4 butterflies per pass.
+template <bool INV, int MAXB>
+__device__ __forceinline__ void stockham(float2* s, const float2* tw, int L, int logL, int nfft,
+                                         int lognfft, int fstride, int estride) {
+  const int q = L >> 2;
+  const int logq = logL - 2;
+  const int total = nfft * q;
+  const bool fmajor = (fstride == 1);
+  int Ns = 1, logNs = 0;
+  for (int pass = 0; pass < (logL >> 1); ++pass) {
+    float2 v[MAXB][4];
+    int ob[MAXB];
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+      const int task = threadIdx.x + b * blockDim.x;
+      if (task < total) {
+        int f, j;
+        if (fmajor) {
+          f = task & (nfft - 1);
+          j = task >> lognfft;
+        } else {
+          f = task >> logq;
+          j = task & (q - 1);
+        }
+        float2* p = s + f * fstride;
+        const int k = j & (Ns - 1);
+        float2 a0 = p[j * estride], a1 = p[(j + q) * estride];
+        float2 a2 = p[(j + 2 * q) * estride], a3 = p[(j + 3 * q) * estride];
+        if (pass > 0) {
+          const int step = k << (logq - logNs);  // k * L / (4 Ns)
+          a1 = cmul(a1, twid<INV>(tw, step));
+          a2 = cmul(a2, twid<INV>(tw, 2 * step));
+          a3 = cmul(a3, twid<INV>(tw, 3 * step));
+        }
+        radix4<INV>(a0, a1, a2, a3);
+        v[b][0] = a0;
+        v[b][1] = a1;
+        v[b][2] = a2;
+        v[b][3] = a3;
+        ob[b] = f * fstride + (((j - k) << 2) + k) * estride;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+      const int task = threadIdx.x + b * blockDim.x;
+      if (task < total) {
+        const int e = Ns * estride;
+        s[ob[b]] = v[b][0];
+        s[ob[b] + e] = v[b][1];
+        s[ob[b] + 2 * e] = v[b][2];
+        s[ob[b] + 3 * e] = v[b][3];
+      }
+    }
+    __syncthreads();
+    Ns <<= 2;
+    logNs += 2;
+  }
+  if (logL & 1) {
+    // last pass, radix 2 with Ns = L/2: reads and writes the same two slots.
+    const int h = L >> 1;
+    const int logh = logL - 1;
+    const int total2 = nfft * h;
+#pragma unroll
+    for (int b = 0; b < 2 * MAXB; ++b) {
+      const int task = threadIdx.x + b * blockDim.x;
+      if (task < total2) {
+        int f, j;
+        if (fmajor) {
+          f = task & (nfft - 1);
+          j = task >> lognfft;
+        } else {
+          f = task >> logh;
+          j = task & (h - 1);
+        }
+        float2* p = s + f * fstride;
+        float2 a0 = p[j * estride];
+        float2 a1 = cmul(p[(j + h) * estride], twid<INV>(tw, j));
+        p[j * estride] = cadd(a0, a1);
+        p[(j + h) * estride] = csub(a0, a1);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- row R2C
+// CTA of T = max(256, M/4) threads transforms R = T / (M/4) consecutive rows.
+template <int MAXB>
+__global__ void __launch_bounds__(512) k_rfft_rows(const float* __restrict__ in, float2* __restrict__ out,
+                                                   long long nrows, int W, int logM) {
+  extern __shared__ float2 sm[];
+  const int M = W >> 1;
+  float2* tw = sm;
+  float2* data = sm + M;
+  const int q = M >> 2;
+  const int R = blockDim.x / q;
+  const long long row0 = (long long)blockIdx.x * R;
+  make_twiddles(tw, M);
+  const long long rows_here = min((long long)R, nrows - row0);
+  const int nf4 = R * (W >> 2);
+  const int valid = (int)rows_here * (W >> 2);
+  const float4* src = reinterpret_cast<const float4*>(in + row0 * W);
+  for (int e = threadIdx.x; e < nf4; e += blockDim.x) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < valid) v = __ldg(src + e);
+    reinterpret_cast<float4*>(data)[e] = v;  // z[n] = x[2n] + i x[2n+1]
+  }
+  __syncthreads();
+  int lognfft = 0;
+  while ((1 << lognfft) < R) ++lognfft;
+  stockham<false, MAXB>(data, tw, M, logM, R, lognfft, M, 1);
+  // Z = E + i O with E, O the DFTs of the even and odd samples;
+  // X[k] = E[k] + exp(-2 pi i k / W) O[k], X[M] = E[0] - O[0].
+  for (int e = threadIdx.x; e < R * M; e += blockDim.x) {
+    const int r = e >> logM, k = e & (M - 1);
+    const long long row = row0 + r;
+    if (row >= nrows) continue;
+    const float2* z = data + r * M;
+    const float2 Zk = z[k];
+    float2 o;
+    if (k == 0) {
+      o = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
+    } else {
+      const float2 Zm = z[M - k];
+      const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+      const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+      float sn, cs;
+      sincospif(-(float)k / (float)M, &sn, &cs);
+      o = cadd(E, cmul(make_float2(cs, sn), O));
+    }
+    out[row * M + k] = o;
+  }
+}
+
+// ---------------------------------------------------------------- row C2R
+template <int MAXB>
+__global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ in, float* __restrict__ out,
+                                                    long long nrows, int H, int W, int logM, float scale,
+                                                    const fdl_request* __restrict__ req,
+                                                    const int* __restrict__ count, int C) {
+  extern __shared__ float2 sm[];
+  const int M = W >> 1;
+  float2* tw = sm;
+  float2* data = sm + M;
+  const int q = M >> 2;
+  const int R = blockDim.x / q;
+  const long long row0 = (long long)blockIdx.x * R;
+  if (count) nrows = min(nrows, (long long)(*count) * C * H);
+  if (row0 >= nrows) return;
+  make_twiddles(tw, M);
+  for (int e = threadIdx.x; e < R * M; e += blockDim.x) {
+    const int r = e >> logM;
+    float2 v = make_float2(0.f, 0.f);
+    if (row0 + r < nrows) v = in[(row0 + r) * M + (e & (M - 1))];
+    data[e] = v;
+  }
+  __syncthreads();
+  // Z[k] = E[k] + i O[k], E[k] = X[k] + conj X[M-k],
+  // O[k] = (X[k] - conj X[M-k]) exp(+2 pi i k / W); X[0], X[M] are packed in element 0.
+  float2 zk[8];
+  int cnt = 0;
+  for (int e = threadIdx.x; e < R * M; e += blockDim.x, ++cnt) {
+    const int r = e >> logM, k = e & (M - 1);
+    const float2* X = data + r * M;
+    float2 Z;
+    if (k == 0) {
+      const float x0 = X[0].x, xm = X[0].y;
+      Z = make_float2(x0 + xm, x0 - xm);
+    } else {
+      const float2 a = X[k], bm = X[M - k];
+      const float2 E = make_float2(a.x + bm.x, a.y - bm.y);
+      float2 O = make_float2(a.x - bm.x, a.y + bm.y);
+      float sn, cs;
+      sincospif((float)k / (float)M, &sn, &cs);
+      O = cmul(O, make_float2(cs, sn));
+      Z = make_float2(E.x - O.y, E.y + O.x);
+    }
+    if (cnt < 8) zk[cnt] = Z;
+  }
+  __syncthreads();
+  cnt = 0;
+  for (int e = threadIdx.x; e < R * M; e += blockDim.x, ++cnt)
+    if (cnt < 8) data[e] = zk[cnt];
+  __syncthreads();
+  int lognfft = 0;
+  while ((1 << lognfft) < R) ++lognfft;
+  stockham<true, MAXB>(data, tw, M, logM, R, lognfft, M, 1);
+  const long long rows_here = min((long long)R, nrows - row0);
+  const int valid = (int)rows_here * (W >> 2);
+  const int logW4 = logM - 1;
+  for (int e = threadIdx.x; e < valid; e += blockDim.x) {
+    float4 v = reinterpret_cast<const float4*>(data)[e];
+    v.x *= scale;
+    v.y *= scale;
+    v.z *= scale;
+    v.w *= scale;
+    const long long row = row0 + (e >> logW4);
+    float* rowp;
+    if (req) {
+      const long long img = row / H;
+      const int y = (int)(row - img * H);
+      const long long b = img / C;
+      const int c = (int)(img - b * C);
+      rowp = req[b].out + ((long long)c * H + y) * W;
+    } else {
+      rowp = out + row * W;
+    }
+    reinterpret_cast<float4*>(rowp)[e & ((W >> 2) - 1)] = v;
+  }
+}
+
+// ---------------------------------------------------------------- columns
+// CTA = one strip of SW columns of one image, all H rows, in shared memory.
+template <bool INV, int MAXB>
+__global__ void __launch_bounds__(512) k_fft_cols(SpecView in, SpecView out, int H, int logH, int W, int SW,
+                                                  int logSW, const int* __restrict__ count, int C) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* data = sm + H;
+  const int c0 = blockIdx.x * SW;
+  const long long img = blockIdx.y;
+  if (count && img >= (long long)(*count) * C) return;
+  make_twiddles(tw, H);
+  const int n = H * SW;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int y = e >> logSW, c = e & (SW - 1);
+    data[e] = in.main[img * in.img_stride + (long long)y * in.pitch + c0 + c];
+  }
+  __syncthreads();
+  if (INV && c0 == 0) {
+    // column 0 <- Herm(F0) + i Herm(FN), Herm(F)[ky] = (F[ky] + conj F[-ky]) / 2
+    float2 pk[8];
+    int cnt = 0;
+    const float2* nyq = in.nyq + img * in.nyq_img_stride;
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x, ++cnt) {
+      const int km = (H - ky) & (H - 1);
+      const float2 f0 = data[ky * SW], f0m = data[km * SW];
+      const float2 fn = nyq[(long long)ky * in.nyq_stride], fnm = nyq[(long long)km * in.nyq_stride];
+      const float2 h0 = make_float2(0.5f * (f0.x + f0m.x), 0.5f * (f0.y - f0m.y));
+      const float2 hn = make_float2(0.5f * (fn.x + fnm.x), 0.5f * (fn.y - fnm.y));
+      if (cnt < 8) pk[cnt] = make_float2(h0.x - hn.y, h0.y + hn.x);
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x, ++cnt)
+      if (cnt < 8) data[ky * SW] = pk[cnt];
+    __syncthreads();
+  }
+  stockham<INV, MAXB>(data, tw, H, logH, SW, logSW, 1, SW);
+  if (!INV && c0 == 0) {
+    // unpack column 0: Z = F0 + i FN with F0, FN DFTs of real columns
+    float2 f0v[8];
+    int cnt = 0;
+    float2* nyq = out.nyq + img * out.nyq_img_stride;
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x, ++cnt) {
+      const int km = (H - ky) & (H - 1);
+      const float2 z = data[ky * SW], zm = data[km * SW];
+      const float2 f0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      const float2 fn = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+      nyq[(long long)ky * out.nyq_stride] = fn;
+      if (cnt < 8) f0v[cnt] = f0;
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x, ++cnt)
+      if (cnt < 8) data[ky * SW] = f0v[cnt];
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int y = e >> logSW, c = e & (SW - 1);
+    out.main[img * out.img_stride + (long long)y * out.pitch + c0 + c] = data[e];
+  }
+}
+
+int strip_width(int H, int W) {
+  int sw = 8192 / H;
+  if (sw > 16) sw = 16;
+  if (sw < 4) sw = 4;
+  if (sw > W / 2) sw = W / 2;
+  return sw;
+}
+
+template <bool INV>
+cudaError_t launch_cols(SpecView in, SpecView out, int nimg, int H, int W, const int* count, int C,
+                        cudaStream_t st) {
+  const int SW = strip_width(H, W);
+  const int T = 512;
+  const int bpt = (SW * H / 4 + T - 1) / T;  // butterflies per thread per pass
+  const size_t smem = (size_t)(H + SW * H) * sizeof(float2);
+  dim3 grid((W / 2) / SW, nimg);
+  const int logH = ilog2(H), logSW = ilog2(SW);
+  cudaError_t e = cudaSuccess;
+#define FDL_COLS(MB)                                                                              \
+  {                                                                                               \
+    e = cudaFuncSetAttribute(k_fft_cols<INV, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             (int)smem);                                                          \
+    if (e != cudaSuccess) return e;                                                               \
+    k_fft_cols<INV, MB><<<grid, T, smem, st>>>(in, out, H, logH, W, SW, logSW, count, C);         \
+  }
+  if (bpt <= 1) FDL_COLS(1)
+  else if (bpt <= 2) FDL_COLS(2)
+  else if (bpt <= 4) FDL_COLS(4)
+  else FDL_COLS(8)
+#undef FDL_COLS
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+cudaError_t launch_rfft_rows(const float* in, float2* out, long long nrows, int W, cudaStream_t st) {
+  const int M = W / 2;
+  const int T = (M / 4 > 256) ? M / 4 : 256;
+  const int R = T / (M / 4);
+  const size_t smem = (size_t)(M + R * M) * sizeof(float2);
+  const long long grid = (nrows + R - 1) / R;
+  cudaError_t e = cudaFuncSetAttribute(k_rfft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_rfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, W, ilog2(M));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int H, int W, float scale,
+                              const fdl_request* req, const int* count, int C, cudaStream_t st) {
+  const int M = W / 2;
+  const int T = (M / 4 > 256) ? M / 4 : 256;
+  const int R = T / (M / 4);
+  const size_t smem = (size_t)(M + R * M) * sizeof(float2);
+  const long long grid = (nrows + R - 1) / R;
+  cudaError_t e = cudaFuncSetAttribute(k_irfft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_irfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, H, W, ilog2(M), scale, req, count, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int W, cudaStream_t st) {
+  return launch_cols<false>(in, out, nimg, H, W, nullptr, 1, st);
+}
+
+cudaError_t launch_fft_cols_inv(SpecView in, float2* out, int nimg, int H, int W, const int* count, int C,
+                                cudaStream_t st) {
+  SpecView o = spec_split(out, nullptr, H, W);
+  return launch_cols<true>(in, o, nimg, H, W, count, C, st);
+}
+
+}  // namespace fdl

@@ -1,0 +1,181 @@
+// High-precision per-frequency solve shared by the layer construction
+// (Sec. V-A) and the calibration gradient (Sec. V-B).  One warp solves one
+// frequency; the matrix lives in shared memory as cx<T>, T = Rdf
+// (double-float) or R64 (native FP64).
+#pragma once
+
+#include "kernels.h"
+
+namespace fdl {
+
+__device__ __forceinline__ void bin_coords(int q, int H, int M, int& ky, int& kx) {
+  const int main_bins = H * M;
+  if (q < main_bins) {
+    ky = q / M;
+    kx = q - ky * M;
+  } else {
+    ky = q - main_bins;
+    kx = M;
+  }
+}
+
+// Gamma^T Gamma of Gamma = tridiag(1, -2, 1), N x N (Eq. 2ndOrderLayer).
+__device__ __forceinline__ float layer2_gtg(int i, int l, int N) {
+  const int dlt = i > l ? i - l : l - i;
+  if (dlt == 0) return 4.f + (i > 0 ? 1.f : 0.f) + (i < N - 1 ? 1.f : 0.f);
+  if (dlt == 1) return -4.f;
+  if (dlt == 2) return 1.f;
+  return 0.f;
+}
+
+// theta = u . w in cycles per unit of disparity
+__device__ __forceinline__ R64 theta_r(float ux, float uy, float wx, float wy, R64) {
+  return {(double)ux * (double)wx + (double)uy * (double)wy};
+}
+__device__ __forceinline__ Rdf theta_r(float ux, float uy, float wx, float wy, Rdf) {
+  return {df_add(two_prod(ux, wx), two_prod(uy, wy))};
+}
+
+// exp(2 pi i t), FP64: CUDA's sincospi after reduction to [-1/2, 1/2].
+__device__ __forceinline__ cx<R64> cexp2pi(R64 t, const float4*) {
+  const double f = t.v - rint(t.v);
+  double s, c;
+  sincospi(2.0 * f, &s, &c);
+  return {{c}, {s}};
+}
+
+// exp(2 pi i t), double-float: t reduced to f in [-1/2, 1/2] and split as
+// f = n/1024 + r (table-driven reduction); exp(2 pi i n/1024) comes from a
+// double-float table, exp(2 pi i r) with |2 pi r| <= pi/1024 from its Taylor
+// series (cos: 1 - x^2/2 + x^4/24, sin: x (1 - x^2/6 + x^4/120); the first
+// omitted terms are below 2^-59).
+__device__ __forceinline__ cx<Rdf> cexp2pi(Rdf t, const float4* tab) {
+  const float nI = rintf(t.v.hi);
+  const df f = two_sum(__fsub_rn(t.v.hi, nI), t.v.lo);
+  const float nf = rintf(f.hi * 1024.f);
+  const int n = (int)nf;
+  const df r = two_sum(__fsub_rn(f.hi, nf * (1.f / 1024.f)), f.lo);
+  const df twopi = {6.28318548202514648f, -1.74845553146951720e-07f};
+  const df x = df_mul(r, twopi);
+  const df x2 = df_mul(x, x);
+  const float x2f = x2.hi;
+  df cs = df_add_f(df_mul_f(x2, -0.5f), x2f * x2f * (1.f / 24.f));
+  cs = df_add_f(cs, 1.f);
+  const df sixth = {0.16666667163372040f, -4.96705387931228900e-09f};
+  df sp = df_add_f(df_neg(df_mul(x2, sixth)), x2f * x2f * (1.f / 120.f));
+  sp = df_add_f(sp, 1.f);
+  const df sn = df_mul(x, sp);
+  const float4 e = __ldg(tab + (n & 1023));
+  const df ec = {e.x, e.y}, es = {e.z, e.w};
+  const df re = df_sub(df_mul(ec, cs), df_mul(es, sn));
+  const df im = df_add(df_mul(ec, sn), df_mul(es, cs));
+  return {{re}, {im}};
+}
+
+struct HpProblem {
+  SpecView b;
+  const float* u;
+  const float* d;
+  const float4* exp_table;
+  int K, C, N, H, W, reg;
+  double lam, lam_eps;
+};
+
+// Shared memory of one warp: G [N][N+1], Arow [N], Y [N][C] (cx<T>).
+template <class T>
+__host__ __device__ __forceinline__ size_t hp_warp_elems(int N, int C) {
+  return (size_t)N * (N + 1) + N + (size_t)N * C;
+}
+
+// Builds G = A*A + lambda Gamma*Gamma and Y = A* b at bin (ky, kx), factors
+// G = L L* in place and overwrites Y with x.  Returns false if a pivot was
+// not positive.  All lanes of the warp must call.
+template <class T>
+__device__ bool hp_solve_bin(const HpProblem& p, int ky, int kx, cx<T>* G, cx<T>* Arow, cx<T>* Y) {
+  const int lane = threadIdx.x & 31;
+  const int N = p.N, C = p.C, M = p.W >> 1;
+  const int ld = N + 1;
+  const T zero = r_from(0.f, T{});
+  const float wy = freq_y(ky, p.H);
+  const float wx = (float)kx / (float)p.W;
+  for (int e = lane; e < N * ld; e += 32) G[e] = {zero, zero};
+  for (int e = lane; e < N * C; e += 32) Y[e] = {zero, zero};
+  __syncwarp();
+  for (int j = 0; j < p.K; ++j) {
+    const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
+    const T th = theta_r(uj.x, uj.y, wx, wy, T{});
+    for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(mulf(th, __ldg(p.d + r)), p.exp_table);
+    __syncwarp();
+    float2 bj[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      bj[c] = c < C ? *p.b.at((long long)j * C + c, ky, kx, M) : make_float2(0.f, 0.f);
+    for (int r = lane; r < N; r += 32) {
+      const cx<T> ar = Arow[r];
+      for (int l = 0; l <= r; ++l) G[r * ld + l] = cx_add(G[r * ld + l], cx_mulc(ar, Arow[l]));
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < C) Y[r * C + c] = cx_add(Y[r * C + c], cx_mulc_f(ar, bj[c]));
+    }
+    __syncwarp();
+  }
+  {
+    const T wxr = r_from(wx, T{}), wyr = r_from(wy, T{});
+    const T w2 = wxr * wxr + wyr * wyr;
+    const T w4 = w2 * w2;
+    const T lam = r_from_double(p.lam, T{});
+    const T lame = r_from_double(p.lam_eps, T{});
+    for (int r = lane; r < N; r += 32) {
+      if (p.reg == 0) {
+        const T dr = r_from(__ldg(p.d + r), T{});
+        const T d2 = dr * dr;
+        G[r * ld + r].re = G[r * ld + r].re + (lam * (w4 * (d2 * d2)) + lame);
+      } else if (p.reg == 1) {
+        for (int l = (r >= 2 ? r - 2 : 0); l <= r; ++l)
+          G[r * ld + l].re = G[r * ld + l].re + mulf(lam, layer2_gtg(r, l, N));
+      } else {
+        G[r * ld + r].re = G[r * ld + r].re + lam;
+      }
+    }
+  }
+  __syncwarp();
+  bool ok = true;
+  const T one = r_from(1.f, T{});
+  for (int k = 0; k < N; ++k) {
+    const T piv = G[k * ld + k].re;
+    const bool pos = r_to_double(piv) > 0.0;
+    ok = ok && pos;
+    const T lkk = r_sqrt(pos ? piv : one);
+    const T inv = one / lkk;
+    __syncwarp();
+    for (int r = lane; r < N; r += 32) {
+      if (r > k) G[r * ld + k] = cx_scale(G[r * ld + k], inv);
+      else if (r == k) G[k * ld + k] = {lkk, zero};
+    }
+    __syncwarp();
+    for (int r = lane; r < N; r += 32) {
+      if (r > k) {
+        const cx<T> lrk = G[r * ld + k];
+        for (int l = k + 1; l <= r; ++l) G[r * ld + l] = cx_sub(G[r * ld + l], cx_mul_conj(lrk, G[l * ld + k]));
+      }
+    }
+    __syncwarp();
+  }
+  if (lane < C) {
+    const int c = lane;
+    for (int k = 0; k < N; ++k) {
+      cx<T> acc = Y[k * C + c];
+      for (int l = 0; l < k; ++l) acc = cx_sub(acc, cx_mul(G[k * ld + l], Y[l * C + c]));
+      Y[k * C + c] = cx_scale(acc, one / G[k * ld + k].re);
+    }
+    for (int k = N - 1; k >= 0; --k) {
+      cx<T> acc = Y[k * C + c];
+      for (int l = k + 1; l < N; ++l) acc = cx_sub(acc, cx_mulc(G[l * ld + k], Y[l * C + c]));
+      Y[k * C + c] = cx_scale(acc, one / G[k * ld + k].re);
+    }
+  }
+  __syncwarp();
+  return ok;
+}
+
+}  // namespace fdl

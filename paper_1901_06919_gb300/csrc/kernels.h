@@ -1,0 +1,80 @@
+// Host-side launchers of the FDL kernels (internal to libfdl).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fdl.h"
+
+namespace fdl {
+
+// ---- FFT (fft.cu) ----------------------------------------------------------
+// Row pass of the 2D real DFT: nrows rows of W floats -> W/2 complex each
+// (element 0 packs X[0] + i X[W/2]), rows written with stride W/2.
+cudaError_t launch_rfft_rows(const float* in, float2* out, long long nrows, int W, cudaStream_t st);
+// Column pass: forward DFT along H of a row-transformed stack held in the
+// split layout `in` (kx = 0 column packed), written unpacked to `out`
+// (may alias `in`).
+cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int W, cudaStream_t st);
+// Inverse column pass: half spectra `in` (any layout) -> split layout `out`
+// with pitch W/2 and the kx = 0 / kx = W/2 columns packed after taking
+// their Hermitian parts.
+// count (nullable, device): only images [0, *count * C) are transformed.
+cudaError_t launch_fft_cols_inv(SpecView in, float2* out, int nimg, int H, int W, const int* count, int C,
+                                cudaStream_t st);
+// Row pass of the inverse real DFT: packed rows (pitch W/2) -> W floats, times scale.
+// req (nullable, device): image b*C + c goes to req[b].out + c*H*W instead of
+// the contiguous `out`; count (nullable, device) limits the images to *count * C.
+cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int H, int W, float scale,
+                              const fdl_request* req, const int* count, int C, cudaStream_t st);
+
+// ---- per-frequency solve (solve.cu) -----------------------------------------
+struct SolveParams {
+  SpecView b;          // input spectra, images ordered [K][C]
+  float2* x;           // output layers, dense [N][C][H][W/2+1]
+  const float* u;      // [K][2]
+  const float* d;      // [N]
+  int K, C, N, H, W;
+  int reg;
+  float lam, lam_eps;  // lambda and lambda*eps
+  double lam_d, lam_eps_d;
+  float kappa_max;
+  int* flagged;        // list of bins for the high-precision pass
+  int* counters;       // [0] fp32 bins, [1] high-precision bins, [2] breakdowns, [3] non-finite, [4] list length
+  const float4* exp_table;  // df table of exp(2 pi i n / 1024), n in [0, 1024)
+};
+cudaError_t launch_solve_f32(const SolveParams& p, bool certify, cudaStream_t st);
+// Solves the bins listed in p.flagged (count in p.counters[4]) or, when
+// all_bins, every stored bin; T = native FP64 when f64 else double-float.
+cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, cudaStream_t st);
+cudaError_t launch_exp_table(float4* table, cudaStream_t st);
+
+// ---- render (render.cu) -----------------------------------------------------
+cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W,
+                                  SpecView out, cudaStream_t st);
+cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N,
+                                    const float* u0, int B, float* out, long long img_elems, cudaStream_t st);
+
+// ---- calibration (calib.cu) -------------------------------------------------
+struct CalibParams {
+  SpecView b;
+  const float* u;
+  const float* d;
+  int K, C, N, H, W;
+  int reg;
+  float lam;
+  const int* bins;     // nullable
+  int nbins;
+  double* partials;    // [kCalibGrid][1 + 2K + N] per-CTA sums (loss, grad_u, grad_d)
+  float* loss;
+  float* grad_u;
+  float* grad_d;
+  int* counters;
+  const float4* exp_table;
+  bool f64;
+  double lam_d;
+};
+constexpr int kCalibGrid = 512;
+cudaError_t launch_calib_grad(const CalibParams& p, cudaStream_t st);
+
+}  // namespace fdl

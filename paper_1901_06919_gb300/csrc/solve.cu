@@ -1,0 +1,363 @@
+// Per-frequency Tikhonov solve of the layer construction (Sec. V-A):
+//   (A*A + lambda Gamma*Gamma) x = A* b,  A_jk = exp(+2 pi i d_k (u_j . w))
+// (Eqs. AMatGeneral, LayerConstructionClosedForm), Gamma*Gamma from Sec. V-C:
+// the view regulariser diag(|w|^4 d^4 + eps) (Eq. 2ndOrderView, plus the
+// epsilon of Sec. V-C1), the layer regulariser tridiag(1,-2,1)^T tridiag(1,-2,1)
+// (Eq. 2ndOrderLayer) or the identity.  The C colour channels share A and
+// Gamma, so one Cholesky factor serves C right-hand sides.
+//
+// Two kernels:
+//  * k_solve_f32: FP32, one warp per frequency, lane i owns row i of the
+//    Hermitian matrix in registers.  It estimates the condition number from
+//    the factor (Gershgorin bound on the largest eigenvalue, three steps of
+//    inverse iteration for the smallest) and keeps the FP32 result only when
+//    the estimate is below kappa_max; other frequencies go to a list.
+//  * k_solve_hp<T>: the same solve in double-float (T = Rdf) or native FP64
+//    (T = R64) for the listed frequencies (or for all of them).
+#include "hp_solve.cuh"
+
+namespace fdl {
+
+namespace {
+
+constexpr int kTileBins = 8;    // bins per CTA tile = warps per CTA
+constexpr int kViewChunk = 32;  // views staged per pass
+
+// ------------------------------------------------------------------ FP32
+template <int NMAX>
+__global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int certify) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int M = p.W >> 1;
+  const int C = p.C, N = p.N, K = p.K;
+  // shared memory carve-up
+  float2* bstage = reinterpret_cast<float2*>(smem4);                  // [kViewChunk*C][kTileBins]
+  float2* arow = bstage + kViewChunk * 4 * kTileBins;                   // [kTileBins][NMAX]
+  float2* Ls = arow + kTileBins * NMAX;                                 // [kTileBins][NMAX][NMAX+1]
+  float2* myA = arow + warp * NMAX;
+  float2* myL = Ls + warp * NMAX * (NMAX + 1);
+  __shared__ int tile_flag[kTileBins];
+  __shared__ int tile_base;
+  __shared__ int cnt_local[4];
+  if (threadIdx.x < 4) cnt_local[threadIdx.x] = 0;
+
+  const int Qs = p.H * (M + 1);
+  const int ntiles = Qs / kTileBins;
+  const float dl = lane < N ? __ldg(p.d + lane) : 0.f;
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int q = tile * kTileBins + warp;
+    int ky, kx;
+    bin_coords(q, p.H, M, ky, kx);
+    const float wy = freq_y(ky, p.H);
+    const float wx = (float)kx / (float)p.W;
+
+    float2 G[NMAX];
+#pragma unroll
+    for (int l = 0; l < NMAX; ++l) G[l] = make_float2(0.f, 0.f);
+    float2 y[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[c] = make_float2(0.f, 0.f);
+    bool finite = true;
+
+    for (int j0 = 0; j0 < K; j0 += kViewChunk) {
+      const int nv = min(kViewChunk, K - j0);
+      __syncthreads();
+      // stage b[j][c][bins of the tile]: consecutive threads read consecutive bins
+      for (int e = threadIdx.x; e < nv * C * kTileBins; e += blockDim.x) {
+        const int img = e / kTileBins, bi = e - img * kTileBins;
+        int qy, qx;
+        bin_coords(tile * kTileBins + bi, p.H, M, qy, qx);
+        bstage[e] = *p.b.at((long long)j0 * C + img, qy, qx, M);
+      }
+      __syncthreads();
+      for (int jj = 0; jj < nv; ++jj) {
+        const int j = j0 + jj;
+        const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
+        float2 a = make_float2(0.f, 0.f);
+        if (lane < N) {
+          const float f = phase_cycles(uj.x, uj.y, wx, wy, dl);
+          sincospif(2.f * f, &a.y, &a.x);
+        }
+        if (lane < NMAX) myA[lane] = a;
+        __syncwarp();
+        const float4* A4 = reinterpret_cast<const float4*>(myA);
+#pragma unroll
+        for (int l2 = 0; l2 < NMAX / 2; ++l2) {
+          const float4 v = A4[l2];
+          cfmac(G[2 * l2], a, make_float2(v.x, v.y));
+          cfmac(G[2 * l2 + 1], a, make_float2(v.z, v.w));
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c < C) {
+            const float2 bv = bstage[(jj * C + c) * kTileBins + warp];
+            finite = finite && isfinite(bv.x) && isfinite(bv.y);
+            cfmac(y[c], a, bv);
+          }
+        }
+        __syncwarp();
+      }
+    }
+
+    // regulariser lambda Gamma*Gamma
+    {
+      const float w2 = wx * wx + wy * wy;
+      const float d2 = dl * dl;
+#pragma unroll
+      for (int l = 0; l < NMAX; ++l) {
+        if (p.reg == 0) {
+          if (l == lane) G[l].x += p.lam * (w2 * w2) * (d2 * d2) + p.lam_eps;
+        } else if (p.reg == 1) {
+          if (lane < N && l < N) G[l].x += p.lam * layer2_gtg(lane, l, N);
+        } else {
+          if (l == lane) G[l].x += p.lam;
+        }
+      }
+    }
+    // Gershgorin bound of the largest eigenvalue
+    float rowsum = 0.f;
+#pragma unroll
+    for (int l = 0; l < NMAX; ++l) rowsum += fabsf(G[l].x) + fabsf(G[l].y);
+    if (lane >= N) rowsum = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rowsum = fmaxf(rowsum, __shfl_xor_sync(0xffffffffu, rowsum, o));
+
+    // Cholesky G = L L*, row i in lane i
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+      if (k < N) {
+        const float piv = __shfl_sync(0xffffffffu, G[k].x, k);
+        ok = ok && (piv > 1e-30f) && isfinite(piv);
+        const float lkk = sqrtf(fmaxf(piv, 1e-30f));
+        const float inv = 1.f / lkk;
+        if (lane > k) G[k] = cscale(G[k], inv);
+        else if (lane == k) G[k] = make_float2(lkk, 0.f);
+        if (lane < NMAX) myA[lane] = G[k];  // column k: L_lk in lane l
+        __syncwarp();
+#pragma unroll
+        for (int l = k + 1; l < NMAX; ++l) {
+          if (l < N && l <= lane) cfms_c(G[l], G[k], myA[l]);
+        }
+        __syncwarp();
+      }
+    }
+    // L to shared memory (row i, pitch NMAX+1)
+#pragma unroll
+    for (int l = 0; l < NMAX; ++l)
+      if (lane < NMAX) myL[lane * (NMAX + 1) + l] = (l <= lane) ? G[l] : make_float2(0.f, 0.f);
+    __syncwarp();
+    const float lii = lane < N ? myL[lane * (NMAX + 1) + lane].x : 1.f;
+
+    // solves: C right-hand sides plus the inverse-iteration vector v
+    float2 v = make_float2(0.f, 0.f);
+    if (lane < N) {
+      float s, c;
+      sincospif(2.f * 0.6180339887f * (float)(lane * lane), &s, &c);
+      v = make_float2(c * rsqrtf((float)N), s * rsqrtf((float)N));
+    }
+    float vnorm = 0.f;
+    for (int it = 0; it < 3; ++it) {
+      // forward: L z = rhs
+      for (int k = 0; k < N; ++k) {
+        const float lkk = __shfl_sync(0xffffffffu, lii, k);
+        const float2 lik = myL[(lane < NMAX ? lane : 0) * (NMAX + 1) + k];
+        const float2 vk = cscale(make_float2(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k)), 1.f / lkk);
+        if (lane > k) cfms_c(v, lik, cconj(vk));
+        else if (lane == k) v = vk;
+        if (it == 0) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (c < C) {
+              const float2 yk = cscale(make_float2(__shfl_sync(0xffffffffu, y[c].x, k),
+                                                   __shfl_sync(0xffffffffu, y[c].y, k)), 1.f / lkk);
+              if (lane > k) cfms_c(y[c], lik, cconj(yk));
+              else if (lane == k) y[c] = yk;
+            }
+          }
+        }
+      }
+      // backward: L* x = z
+      for (int k = N - 1; k >= 0; --k) {
+        const float lkk = __shfl_sync(0xffffffffu, lii, k);
+        const float2 lki = myL[k * (NMAX + 1) + (lane < NMAX ? lane : 0)];  // L_ki
+        const float2 vk = cscale(make_float2(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k)), 1.f / lkk);
+        if (lane < k) cfms_c(v, cconj(lki), cconj(vk));  // v_i -= conj(L_ki) x_k
+        else if (lane == k) v = vk;
+        if (it == 0) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (c < C) {
+              const float2 yk = cscale(make_float2(__shfl_sync(0xffffffffu, y[c].x, k),
+                                                   __shfl_sync(0xffffffffu, y[c].y, k)), 1.f / lkk);
+              if (lane < k) cfms_c(y[c], cconj(lki), cconj(yk));
+              else if (lane == k) y[c] = yk;
+            }
+          }
+        }
+      }
+      float n2 = lane < N ? v.x * v.x + v.y * v.y : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      vnorm = sqrtf(n2);
+      const float inv = vnorm > 0.f ? 1.f / vnorm : 0.f;
+      v = cscale(v, inv);
+    }
+    const float kappa = rowsum * vnorm;
+    const bool keep = !certify || (ok && finite && kappa <= p.kappa_max && isfinite(kappa));
+    // without certification a factorisation that broke down leaves zeros
+    const bool broke = !certify && !ok;
+    if (keep && lane < N) {
+      const long long plane = (long long)p.H * (M + 1);
+      const long long off = (long long)ky * (M + 1) + kx;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < C) p.x[((long long)lane * C + c) * plane + off] = broke ? make_float2(0.f, 0.f) : y[c];
+    }
+    // tile bookkeeping: one atomic per tile for the list
+    if (lane == 0) {
+      tile_flag[warp] = keep ? 0 : 1;
+      if (keep && !broke) atomicAdd(&cnt_local[0], 1);
+      if (broke) atomicAdd(&cnt_local[2], 1);
+      if (!finite) atomicAdd(&cnt_local[3], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int nf = 0;
+      for (int w = 0; w < kTileBins; ++w) nf += tile_flag[w];
+      tile_base = nf ? atomicAdd(p.counters + 4, nf) : 0;
+    }
+    __syncthreads();
+    if (lane == 0 && tile_flag[warp]) {
+      int pos = tile_base;
+      for (int w = 0; w < warp; ++w) pos += tile_flag[w];
+      p.flagged[pos] = q;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (cnt_local[0]) atomicAdd(p.counters + 0, cnt_local[0]);
+    if (cnt_local[2]) atomicAdd(p.counters + 2, cnt_local[2]);
+    if (cnt_local[3]) atomicAdd(p.counters + 3, cnt_local[3]);
+  }
+}
+
+// --------------------------------------------------------- high precision
+template <class T>
+__global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, int warps) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int M = sp.W >> 1;
+  HpProblem p;
+  p.b = sp.b;
+  p.u = sp.u;
+  p.d = sp.d;
+  p.exp_table = sp.exp_table;
+  p.K = sp.K;
+  p.C = sp.C;
+  p.N = sp.N;
+  p.H = sp.H;
+  p.W = sp.W;
+  p.reg = sp.reg;
+  p.lam = sp.lam_d;
+  p.lam_eps = sp.lam_eps_d;
+  const int N = p.N, C = p.C;
+  cx<T>* G = reinterpret_cast<cx<T>*>(smem4) + warp * hp_warp_elems<T>(N, C);
+  cx<T>* Arow = G + N * (N + 1);
+  cx<T>* Y = Arow + N;
+  const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(sp.counters + 4));
+  int nhp = 0, nbad = 0;
+  for (int li = blockIdx.x * warps + warp; li < total; li += gridDim.x * warps) {
+    const int q = all_bins ? li : sp.flagged[li];
+    int ky, kx;
+    bin_coords(q, p.H, M, ky, kx);
+    const bool ok = hp_solve_bin<T>(p, ky, kx, G, Arow, Y);
+    const long long plane = (long long)p.H * (M + 1);
+    const long long off = (long long)ky * (M + 1) + kx;
+    for (int e = lane; e < N * C; e += 32) {
+      const int r = e / C, c = e - r * C;
+      const cx<T> v = Y[e];
+      sp.x[((long long)r * C + c) * plane + off] =
+          ok ? make_float2(r_to_float(v.re), r_to_float(v.im)) : make_float2(0.f, 0.f);
+    }
+    if (lane == 0) {
+      ++nhp;
+      if (!ok) ++nbad;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (nhp) atomicAdd(sp.counters + 1, nhp);
+    if (nbad) atomicAdd(sp.counters + 2, nbad);
+  }
+}
+
+__global__ void k_exp_table(float4* tab) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < 1024) {
+    double s, c;
+    sincospi(2.0 * (double)n / 1024.0, &s, &c);
+    const float ch = (float)c, sh = (float)s;
+    tab[n] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+  }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
+template <int NMAX>
+cudaError_t launch_f32_n(const SolveParams& p, bool certify, cudaStream_t st) {
+  const size_t smem = (size_t)(kViewChunk * 4 * kTileBins + kTileBins * NMAX +
+                               kTileBins * NMAX * (NMAX + 1)) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_solve_f32<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int ntiles = p.H * (p.W / 2 + 1) / kTileBins;
+  int grid = num_sms() * 4;
+  if (grid > ntiles) grid = ntiles;
+  k_solve_f32<NMAX><<<grid, kTileBins * 32, smem, st>>>(p, certify ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_hp_t(const SolveParams& p, bool all_bins, cudaStream_t st) {
+  const size_t per_warp = hp_warp_elems<T>(p.N, p.C) * sizeof(cx<T>);
+  int warps = (int)(96 * 1024 / per_warp);
+  if (warps > 4) warps = 4;
+  if (warps < 1) warps = 1;
+  const size_t smem = per_warp * warps;
+  cudaError_t e = cudaFuncSetAttribute(k_solve_hp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = num_sms() * 8;
+  k_solve_hp<T><<<grid, warps * 32, smem, st>>>(p, all_bins ? 1 : 0, warps);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_solve_f32(const SolveParams& p, bool certify, cudaStream_t st) {
+  if (p.N <= 8) return launch_f32_n<8>(p, certify, st);
+  if (p.N <= 16) return launch_f32_n<16>(p, certify, st);
+  return launch_f32_n<32>(p, certify, st);
+}
+
+cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, cudaStream_t st) {
+  return f64 ? launch_hp_t<R64>(p, all_bins, st) : launch_hp_t<Rdf>(p, all_bins, st);
+}
+
+cudaError_t launch_exp_table(float4* table, cudaStream_t st) {
+  k_exp_table<<<4, 256, 0, st>>>(table);
+  return cudaGetLastError();
+}
+
+}  // namespace fdl

@@ -8,3 +8,22 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def fdl():
+    """The CUDA binding, with libfdl.so built for this machine (GPU tests only)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1901_06919_gb300 import build as B
+
+    B.build()
+    import paper_1901_06919_gb300 as F
+
+    F.load()
+    return F

@@ -100,3 +100,13 @@ def test_image_from_half_takes_real_part_of_completed_spectrum():
 def test_frequency_convention():
     assert np.allclose(O.freq_y(8), [0, 1 / 8, 2 / 8, 3 / 8, -4 / 8, -3 / 8, -2 / 8, -1 / 8])
     assert np.allclose(O.freq_x_half(8), [0, 1 / 8, 2 / 8, 3 / 8, 4 / 8])
+
+
+def test_dft_at_bins_is_the_definition():
+    rng = np.random.default_rng(5)
+    img = rng.random((2, 16, 32))
+    ky = np.array([0, 3, 8, 15])
+    kx = np.array([0, 7, 16, 5])
+    ref = np.fft.fft2(img)[:, ky, kx]
+    assert np.allclose(O.dft_at_bins(img, ky, kx), ref, atol=1e-11)
+    assert np.allclose(O.dft_at_bins(img, ky, kx), O.dft2(img)[:, ky, kx], atol=1e-11)
