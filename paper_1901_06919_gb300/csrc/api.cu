@@ -94,22 +94,26 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
   if (e != cudaSuccess) return FDL_ECUDA;
   e = launch_exp_table(f.exp_table, st);
   if (e != cudaSuccess) return FDL_ECUDA;
+  // double-float: registers for N <= 48, shared memory beyond
+  auto solve_df = [&](bool all_bins) {
+    return solve_df_supported(N) ? launch_solve_df(p, all_bins, st) : launch_solve_hp(p, all_bins, false, st);
+  };
   switch (o->precision) {
     case FDL_PREC_F32:
       e = launch_solve_f32(p, false, st);
       break;
     case FDL_PREC_DF:
-      e = launch_solve_hp(p, true, false, st);
+      e = solve_df(true);
       break;
     case FDL_PREC_F64:
       e = launch_solve_hp(p, true, true, st);
       break;
     default:
       if (N > 32) {
-        e = launch_solve_hp(p, true, false, st);
+        e = solve_df(true);
       } else {
         e = launch_solve_f32(p, true, st);
-        if (e == cudaSuccess) e = launch_solve_hp(p, false, false, st);
+        if (e == cudaSuccess) e = solve_df(false);
       }
   }
   return cuda_status(e);

@@ -48,6 +48,10 @@ cudaError_t launch_solve_f32(const SolveParams& p, bool certify, cudaStream_t st
 // all_bins, every stored bin; T = native FP64 when f64 else double-float.
 cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, cudaStream_t st);
 cudaError_t launch_exp_table(float4* table, cudaStream_t st);
+// Double-float solve with the matrix in registers (N <= 48); same contract as
+// launch_solve_hp with f64 = false.
+bool solve_df_supported(int N);
+cudaError_t launch_solve_df(const SolveParams& p, bool all_bins, cudaStream_t st);
 
 // ---- render (render.cu) -----------------------------------------------------
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W,

@@ -1,0 +1,377 @@
+// Double-float per-frequency solve with the matrix in registers.
+//
+// Same problem as k_solve_hp<Rdf> (Sec. V-A, Eqs. AMatGeneral and
+// LayerConstructionClosedForm with the Sec. V-C regularisers), organised for
+// the FP32 pipe of sm_103a:
+//  * one warp per frequency; the N(N+1)/2 entries of the lower triangle of
+//    A*A + lambda Gamma*Gamma are numbered column by column and entry e lives
+//    in lane e % 32, register slot e / 32, so every lane holds about the same
+//    number of entries;
+//  * A_jk = hi + lo (double-float); the Gram sum over views takes the hi*hi
+//    products exactly (TwoProd), adds them with TwoSum and collects every
+//    rounding error, plus the hi*lo cross terms, in the low word;
+//  * Cholesky runs on the register slots with the pivot column broadcast
+//    through shared memory; the triangular solves run one row per lane.
+#include "hp_solve.cuh"
+
+namespace fdl {
+
+namespace {
+
+constexpr int kDfWarps = 4;
+#ifndef FDL_DF_MINBLOCKS
+#define FDL_DF_MINBLOCKS 2
+#endif
+
+// entry (r, l), l <= r, numbered column-major: column l starts at l*N - l(l-1)/2
+__device__ __forceinline__ int col_start(int l, int N) { return l * N - (l * (l - 1)) / 2; }
+
+struct dfc {
+  df re, im;
+};
+
+__device__ __forceinline__ float4 pack(const dfc& a) { return make_float4(a.re.hi, a.im.hi, a.re.lo, a.im.lo); }
+__device__ __forceinline__ dfc unpack(float4 v) { return {{v.x, v.z}, {v.y, v.w}}; }
+
+// acc += conj(a) * b for a, b double-float complex stored as (re.hi, im.hi, re.lo, im.lo);
+// acc's low words collect the rounding errors (renormalised by the caller).
+__device__ __forceinline__ void gram_acc(dfc& g, float4 a, float4 b) {
+  // real part: a.hx b.hx + a.hy b.hy (+ cross terms)
+  {
+    const float p1 = __fmul_rn(a.x, b.x), e1 = fmaf(a.x, b.x, -p1);
+    const float p2 = __fmul_rn(a.y, b.y), e2 = fmaf(a.y, b.y, -p2);
+    const df s1 = two_sum(g.re.hi, p1);
+    const df s2 = two_sum(s1.hi, p2);
+    float lo = g.re.lo + (s1.lo + s2.lo) + (e1 + e2);
+    lo = fmaf(a.x, b.z, lo);
+    lo = fmaf(a.y, b.w, lo);
+    lo = fmaf(a.z, b.x, lo);
+    lo = fmaf(a.w, b.y, lo);
+    g.re = {s2.hi, lo};
+  }
+  // imaginary part: a.hx b.hy - a.hy b.hx (+ cross terms)
+  {
+    const float q1 = __fmul_rn(a.x, b.y), f1 = fmaf(a.x, b.y, -q1);
+    const float q2 = __fmul_rn(a.y, b.x), f2 = fmaf(a.y, b.x, -q2);
+    const df s1 = two_sum(g.im.hi, q1);
+    const df s2 = two_sum(s1.hi, -q2);
+    float lo = g.im.lo + (s1.lo + s2.lo) + (f1 - f2);
+    lo = fmaf(a.x, b.w, lo);
+    lo = fmaf(-a.y, b.z, lo);
+    lo = fmaf(a.z, b.y, lo);
+    lo = fmaf(-a.w, b.x, lo);
+    g.im = {s2.hi, lo};
+  }
+}
+
+// the low word may exceed a high word that cancelled, so TwoSum, not Fast2Sum
+__device__ __forceinline__ void renorm(dfc& g) {
+  g.re = two_sum(g.re.hi, g.re.lo);
+  g.im = two_sum(g.im.hi, g.im.lo);
+}
+
+// hi*hi product of two double-float reals, exact (p + e), plus the hi*lo cross terms in x
+struct prod3 {
+  float p, e, x;
+};
+__device__ __forceinline__ prod3 mul3(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = fmaf(a.hi, b.hi, -p);
+  const float x = fmaf(a.hi, b.lo, a.lo * b.hi);
+  return {p, e, x};
+}
+// g + s1 * u + s2 * v (s1, s2 = +-1 folded into the products), compensated and renormalised
+__device__ __forceinline__ df acc2(df g, prod3 u, prod3 v) {
+  const df t1 = two_sum(g.hi, u.p);
+  const df t2 = two_sum(t1.hi, v.p);
+  const float lo = g.lo + (t1.lo + t2.lo) + ((u.e + v.e) + (u.x + v.x));
+  return fast_two_sum(t2.hi, lo);
+}
+__device__ __forceinline__ prod3 neg3(prod3 a) { return {-a.p, -a.e, -a.x}; }
+
+// g -= a * conj(b): re -= a.re b.re + a.im b.im, im -= a.im b.re - a.re b.im
+__device__ __forceinline__ void sub_mul_conj(dfc& g, const dfc& a, const dfc& b) {
+  g.re = acc2(g.re, neg3(mul3(a.re, b.re)), neg3(mul3(a.im, b.im)));
+  g.im = acc2(g.im, neg3(mul3(a.im, b.re)), mul3(a.re, b.im));
+}
+
+// g -= a * b: re -= a.re b.re - a.im b.im, im -= a.re b.im + a.im b.re
+__device__ __forceinline__ void sub_mul(dfc& g, const dfc& a, const dfc& b) {
+  g.re = acc2(g.re, neg3(mul3(a.re, b.re)), mul3(a.im, b.im));
+  g.im = acc2(g.im, neg3(mul3(a.re, b.im)), neg3(mul3(a.im, b.re)));
+}
+
+// g -= conj(a) * b: re -= a.re b.re + a.im b.im, im -= a.re b.im - a.im b.re
+__device__ __forceinline__ void sub_conj_mul(dfc& g, const dfc& a, const dfc& b) {
+  g.re = acc2(g.re, neg3(mul3(a.re, b.re)), neg3(mul3(a.im, b.im)));
+  g.im = acc2(g.im, neg3(mul3(a.re, b.im)), mul3(a.im, b.re));
+}
+
+__device__ __forceinline__ dfc scale(const dfc& a, df s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
+
+// y += conj(a) * b for a double-float (re.hi, im.hi, re.lo, im.lo), b single precision
+__device__ __forceinline__ void rhs_acc(dfc& y, float4 a, float2 b) {
+  const df are = {a.x, a.z}, aim = {a.y, a.w}, br = {b.x, 0.f}, bi = {b.y, 0.f};
+  y.re = acc2(y.re, mul3(are, br), mul3(aim, bi));
+  y.im = acc2(y.im, mul3(are, bi), neg3(mul3(aim, br)));
+}
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+template <int NMAX, int S>
+__global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(SolveParams p, int all_bins) {
+  constexpr int R = (NMAX + 31) / 32;  // rows per lane in the solves
+  extern __shared__ float4 sm4[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int N = p.N, C = p.C, K = p.K, M = p.W >> 1;
+  const int E = N * (N + 1) / 2;
+  float4* Arow = sm4 + warp * (2 * NMAX + NMAX * (NMAX + 1) / 2 + NMAX);
+  float4* col = Arow + NMAX;
+  float4* Ls = col + NMAX;                       // packed lower triangle, column-major
+  float2* invd = reinterpret_cast<float2*>(Ls + NMAX * (NMAX + 1) / 2);  // 1 / L_kk as df
+
+  // coordinates (r, l) of this lane's slots, packed as r * 256 + l (-1: unused slot)
+  int rl[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = lane + 32 * s;
+    rl[s] = -1;
+    if (e < E) {
+      int l = 0;
+      while (col_start(l + 1, N) <= e) ++l;
+      rl[s] = ((l + (e - col_start(l, N))) << 8) | l;
+    }
+  }
+#define SR(s) (rl[s] >> 8)
+#define SL(s) (rl[s] < 0 ? -1 : (rl[s] & 255))
+  const float4* tab = p.exp_table;
+  const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(p.counters + 4));
+  int nhp = 0, nbad = 0;
+  for (int li = blockIdx.x * kDfWarps + warp; li < total; li += gridDim.x * kDfWarps) {
+    const int q = all_bins ? li : p.flagged[li];
+    int ky, kx;
+    bin_coords(q, p.H, M, ky, kx);
+    const float wy = freq_y(ky, p.H);
+    const float wx = (float)kx / (float)p.W;
+
+    dfc G[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) G[s] = {{0.f, 0.f}, {0.f, 0.f}};
+    dfc y[R][4];
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y[h][c] = {{0.f, 0.f}, {0.f, 0.f}};
+
+    float dr[R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) dr[h] = (lane + 32 * h < N) ? __ldg(p.d + lane + 32 * h) : 0.f;
+
+    for (int j = 0; j < K; ++j) {
+      const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
+      const Rdf th = theta_r(uj.x, uj.y, wx, wy, Rdf{});
+      float2 bj[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bj[c] = c < C ? *p.b.at((long long)j * C + c, ky, kx, M) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < R; ++h) {
+        const int r = lane + 32 * h;
+        if (r < N) {
+          const cx<Rdf> a = cexp2pi(mulf(th, dr[h]), tab);
+          const float4 av = make_float4(a.re.v.hi, a.im.v.hi, a.re.v.lo, a.im.v.lo);
+          Arow[r] = av;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c < C) rhs_acc(y[h][c], av, bj[c]);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        if (SR(s) > SL(s)) {  // off-diagonal: the diagonal sum of |A_jk|^2 is exactly K
+          gram_acc(G[s], Arow[SR(s)], Arow[SL(s)]);
+          // keep |lo| within an ulp of |hi| so that the low word's own rounding stays at 2^-48
+          G[s].re = fast_two_sum(G[s].re.hi, G[s].re.lo);
+          G[s].im = fast_two_sum(G[s].im.hi, G[s].im.lo);
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      renorm(G[s]);
+      if (SR(s) >= 0 && SR(s) == SL(s)) G[s] = {{(float)K, 0.f}, {0.f, 0.f}};
+    }
+
+    // lambda Gamma*Gamma
+    {
+      const df w2 = df_add(two_prod(wx, wx), two_prod(wy, wy));
+      const df w4 = df_mul(w2, w2);
+      const df lam = df_from_double(p.lam_d);
+      const df lame = df_from_double(p.lam_eps_d);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int r = SR(s), l = SL(s);
+        if (r < 0) continue;
+        if (p.reg == 0) {
+          if (r == l) {
+            const float dv = __ldg(p.d + r);
+            const df d2 = two_prod(dv, dv);
+            G[s].re = df_add(G[s].re, df_add(df_mul(lam, df_mul(w4, df_mul(d2, d2))), lame));
+          }
+        } else if (p.reg == 1) {
+          if (r - l <= 2) G[s].re = df_add(G[s].re, df_mul_f(lam, layer2_gtg(r, l, N)));
+        } else if (r == l) {
+          G[s].re = df_add(G[s].re, lam);
+        }
+      }
+    }
+
+    // Cholesky on the slots
+    bool ok = true;
+    for (int k = 0; k < N; ++k) {
+      // the owner of (k, k) publishes the pivot
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (SR(s) == k && SL(s) == k) col[k] = make_float4(G[s].re.hi, 0.f, G[s].re.lo, 0.f);
+      __syncwarp();
+      const float4 pv = col[k];
+      const df piv = {pv.x, pv.z};
+      ok = ok && (piv.hi > 0.f);
+      const df lkk = df_sqrt(piv.hi > 0.f ? piv : df_from(1.f));
+      const df inv = df_div(df_from(1.f), lkk);
+      if (lane == 0) invd[k] = make_float2(inv.hi, inv.lo);
+      __syncwarp();
+      // scale column k and publish it
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        if (SL(s) == k) {
+          if (SR(s) == k) {
+            G[s] = {lkk, {0.f, 0.f}};
+          } else {
+            G[s] = scale(G[s], inv);
+          }
+          col[SR(s)] = pack(G[s]);
+        }
+      }
+      __syncwarp();
+      // trailing update G_rl -= L_rk conj(L_lk), l > k
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (SL(s) > k) sub_mul_conj(G[s], unpack(col[SR(s)]), unpack(col[SL(s)]));
+      __syncwarp();
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (SR(s) >= 0) Ls[lane + 32 * s] = pack(G[s]);
+    __syncwarp();
+
+    // forward substitution L z = y, row r in lane r % 32
+    for (int k = 0; k < N; ++k) {
+      const float2 iv = invd[k];
+      const df inv = {iv.x, iv.y};
+      const int owner = k & 31, hk = k >> 5;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < C) {
+          float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < R; ++h)
+            if (h == hk) mine = pack(y[h][c]);
+          const dfc zk = scale(unpack(shfl4(mine, owner)), inv);
+#pragma unroll
+          for (int h = 0; h < R; ++h) {
+            const int r = lane + 32 * h;
+            if (r > k && r < N) sub_mul(y[h][c], unpack(Ls[col_start(k, N) + (r - k)]), zk);
+            else if (r == k) y[h][c] = zk;
+          }
+        }
+      }
+    }
+    // back substitution L* x = z
+    for (int k = N - 1; k >= 0; --k) {
+      const float2 iv = invd[k];
+      const df inv = {iv.x, iv.y};
+      const int owner = k & 31, hk = k >> 5;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < C) {
+          float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < R; ++h)
+            if (h == hk) mine = pack(y[h][c]);
+          const dfc xk = scale(unpack(shfl4(mine, owner)), inv);
+#pragma unroll
+          for (int h = 0; h < R; ++h) {
+            const int r = lane + 32 * h;
+            // x_r -= conj(L_kr) x_k for r < k; L_kr is entry (k, r) of column r
+            if (r < k) sub_conj_mul(y[h][c], unpack(Ls[col_start(r, N) + (k - r)]), xk);
+            else if (r == k) y[h][c] = xk;
+          }
+        }
+      }
+    }
+    const long long plane = (long long)p.H * (M + 1);
+    const long long off = (long long)ky * (M + 1) + kx;
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+      const int r = lane + 32 * h;
+      if (r < N) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < C)
+            p.x[((long long)r * C + c) * plane + off] =
+                ok ? make_float2(y[h][c].re.hi + y[h][c].re.lo, y[h][c].im.hi + y[h][c].im.lo) : make_float2(0.f, 0.f);
+      }
+    }
+    if (lane == 0) {
+      ++nhp;
+      if (!ok) ++nbad;
+    }
+    __syncwarp();
+  }
+#undef SR
+#undef SL
+  if (lane == 0) {
+    if (nhp) atomicAdd(p.counters + 1, nhp);
+    if (nbad) atomicAdd(p.counters + 2, nbad);
+  }
+}
+
+template <int NMAX, int S>
+cudaError_t launch_df_n(const SolveParams& p, bool all_bins, cudaStream_t st) {
+  const size_t per_warp = (size_t)(2 * NMAX + NMAX * (NMAX + 1) / 2 + NMAX) * sizeof(float4);
+  const size_t smem = per_warp * kDfWarps;
+  cudaError_t e = cudaFuncSetAttribute(k_solve_df<NMAX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_solve_df<NMAX, S><<<sms * 8, kDfWarps * 32, smem, st>>>(p, all_bins ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool solve_df_supported(int N) { return N <= 48; }
+
+cudaError_t launch_solve_df(const SolveParams& p, bool all_bins, cudaStream_t st) {
+  // register slots per lane: ceil(NMAX (NMAX + 1) / 64)
+  if (p.N <= 8) return launch_df_n<8, 2>(p, all_bins, st);
+  if (p.N <= 12) return launch_df_n<12, 3>(p, all_bins, st);
+  if (p.N <= 16) return launch_df_n<16, 5>(p, all_bins, st);
+  if (p.N <= 20) return launch_df_n<20, 7>(p, all_bins, st);
+  if (p.N <= 24) return launch_df_n<24, 10>(p, all_bins, st);
+  if (p.N <= 28) return launch_df_n<28, 13>(p, all_bins, st);
+  if (p.N <= 30) return launch_df_n<30, 15>(p, all_bins, st);
+  if (p.N <= 32) return launch_df_n<32, 17>(p, all_bins, st);
+  if (p.N <= 36) return launch_df_n<36, 21>(p, all_bins, st);
+  if (p.N <= 40) return launch_df_n<40, 26>(p, all_bins, st);
+  if (p.N <= 44) return launch_df_n<44, 31>(p, all_bins, st);
+  return launch_df_n<48, 37>(p, all_bins, st);
+}
+
+}  // namespace fdl
