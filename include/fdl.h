@@ -139,6 +139,24 @@ FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W,
                             float* layers, void* workspace, size_t workspace_bytes,
                             void* stream);
 
+/* fdl_fit_spectra without a workspace, for callers that may not allocate device
+ * memory: code running while a stream is being captured into a CUDA graph,
+ * real-time loops that cannot afford cudaMalloc's implicit synchronisation,
+ * and hosts (plugins, renderers, frameworks with their own caching allocator)
+ * that own the whole device-memory budget and forbid allocations by libraries.
+ * The paper has no counterpart: this is an integration variant only.
+ * Its scratch is a fixed array inside the library (2,117,888 bytes on every
+ * GPU that loads it, held until the process exits); H * (W/2 + 1) must not
+ * exceed 525,312 (a 1024 x 1024 image), otherwise FDL_ENOMEM.  The first call
+ * on each device looks up the array's device address, so make it before any
+ * stream capture.  All calls on a device share the array: calls that may run
+ * at the same time on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller.  The counters of
+ * fdl_fit_tier_counts are not available for this variant. */
+FDL_API int fdl_fit_spectra_noalloc(const float* spectra, int K, int C, int H, int W, const float* u,
+                                    const float* d, int N, const fdl_fit_opts* opts, float* layers,
+                                    void* stream);
+
 /* After fdl_fit / fdl_fit_spectra on `stream`: counts[0] = frequencies solved
  * in FP32, counts[1] = frequencies solved in double-float or FP64, counts[2]
  * = frequencies whose high-precision factorisation broke down (left as

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -336,3 +337,60 @@ FDL_API int fdl_calib_grad(const float* spectra, int K, int C, int H, int W, con
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ fixed-scratch fit
+// Scratch of fdl_fit_spectra_noalloc: a file-scope device array, so that the
+// entry point never allocates.  Every GPU that loads the library holds it
+// (2,117,888 bytes) until the process exits; all calls on a device share it.
+namespace {
+
+constexpr size_t kNoAllocMaxBins = 1024 * 513;  // H * (W/2 + 1) of a 1024 x 1024 image
+constexpr size_t kNoAllocCounters = 256;
+constexpr size_t kNoAllocTable = 1024 * sizeof(float4);
+constexpr size_t kNoAllocBytes = kNoAllocCounters + kNoAllocTable + kNoAllocMaxBins * sizeof(int);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per device.
+// Host code must not hand the symbol itself to a kernel: on the host it only
+// names a stand-in object.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return FDL_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FDL_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FDL_OK;
+}
+
+}  // namespace
+
+extern "C" FDL_API int fdl_fit_spectra_noalloc(const float* spectra, int K, int C, int H, int W, const float* u,
+                                               const float* d, int N, const fdl_fit_opts* opts, float* layers,
+                                               void* stream) {
+  int s = check_fit_args(K, C, H, W, N, opts);
+  if (s != FDL_OK) return s;
+  if (!spectra || !u || !d || !layers) return FDL_EINVAL;
+  if ((size_t)H * (W / 2 + 1) > kNoAllocMaxBins) return FDL_ENOMEM;
+  void* base = nullptr;
+  s = noalloc_scratch(&base);
+  if (s != FDL_OK) return s;
+  char* b = static_cast<char*>(base);
+  FitWs f;
+  f.counters = reinterpret_cast<int*>(b);
+  f.exp_table = reinterpret_cast<float4*>(b + kNoAllocCounters);
+  f.flagged = reinterpret_cast<int*>(b + kNoAllocCounters + kNoAllocTable);
+  f.spec_main = f.spec_nyq = nullptr;
+  f.bytes = kNoAllocBytes;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SpecView bv = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
+  return run_solve(bv, K, C, H, W, u, d, N, opts, layers, f, st);
+}
