@@ -140,7 +140,7 @@ template <class T>
 cudaError_t launch_t(const CalibParams& p, cudaStream_t st) {
   const size_t pw = hp_warp_elems<T>(p.N, p.C) + 4;
   const size_t smem = kCalibWarps * pw * sizeof(cx<T>) + (size_t)kCalibWarps * (1 + 2 * p.K + p.N) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_calib<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem((const void*)k_calib<T>, smem);
   if (e != cudaSuccess) return e;
   k_calib<T><<<kCalibGrid, kCalibWarps * 32, smem, st>>>(p);
   e = cudaGetLastError();

@@ -10,6 +10,9 @@
 // Every FFT here is a Stockham autosort FFT (radix 4, one radix-2 pass when
 // log2 L is odd) run by a whole CTA on data staged in shared memory.
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.h"
 
@@ -340,8 +343,7 @@ cudaError_t launch_cols(SpecView in, SpecView out, int nimg, int H, int W, const
   cudaError_t e = cudaSuccess;
 #define FDL_COLS(MB)                                                                              \
   {                                                                                               \
-    e = cudaFuncSetAttribute(k_fft_cols<INV, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                             (int)smem);                                                          \
+    e = set_smem((const void*)k_fft_cols<INV, MB>, smem);                                         \
     if (e != cudaSuccess) return e;                                                               \
     k_fft_cols<INV, MB><<<grid, T, smem, st>>>(in, out, H, logH, W, SW, logSW, count, C);         \
   }
@@ -355,6 +357,20 @@ cudaError_t launch_cols(SpecView in, SpecView out, int nimg, int H, int W, const
 
 }  // namespace
 
+cudaError_t set_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[{kernel, dev}];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
 int ilog2(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
@@ -367,7 +383,7 @@ cudaError_t launch_rfft_rows(const float* in, float2* out, long long nrows, int 
   const int R = T / (M / 4);
   const size_t smem = (size_t)(M + R * M) * sizeof(float2);
   const long long grid = (nrows + R - 1) / R;
-  cudaError_t e = cudaFuncSetAttribute(k_rfft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem((const void*)k_rfft_rows<1>, smem);
   if (e != cudaSuccess) return e;
   k_rfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, W, ilog2(M));
   return cudaGetLastError();
@@ -380,7 +396,7 @@ cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int
   const int R = T / (M / 4);
   const size_t smem = (size_t)(M + R * M) * sizeof(float2);
   const long long grid = (nrows + R - 1) / R;
-  cudaError_t e = cudaFuncSetAttribute(k_irfft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem((const void*)k_irfft_rows<1>, smem);
   if (e != cudaSuccess) return e;
   k_irfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, H, W, ilog2(M), scale, req, count, C);
   return cudaGetLastError();

@@ -8,6 +8,10 @@
 
 namespace fdl {
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device; the attribute is set once per (kernel, device, size).
+cudaError_t set_smem(const void* kernel, size_t bytes);
+
 // ---- FFT (fft.cu) ----------------------------------------------------------
 // Row pass of the 2D real DFT: nrows rows of W floats -> W/2 complex each
 // (element 0 packs X[0] + i X[W/2]), rows written with stride W/2.

@@ -320,7 +320,7 @@ template <int NMAX>
 cudaError_t launch_f32_n(const SolveParams& p, bool certify, cudaStream_t st) {
   const size_t smem = (size_t)(kViewChunk * 4 * kTileBins + kTileBins * NMAX +
                                kTileBins * NMAX * (NMAX + 1)) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_solve_f32<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem((const void*)k_solve_f32<NMAX>, smem);
   if (e != cudaSuccess) return e;
   const int ntiles = p.H * (p.W / 2 + 1) / kTileBins;
   int grid = num_sms() * 4;
@@ -336,7 +336,7 @@ cudaError_t launch_hp_t(const SolveParams& p, bool all_bins, cudaStream_t st) {
   if (warps > 4) warps = 4;
   if (warps < 1) warps = 1;
   const size_t smem = per_warp * warps;
-  cudaError_t e = cudaFuncSetAttribute(k_solve_hp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem((const void*)k_solve_hp<T>, smem);
   if (e != cudaSuccess) return e;
   const int grid = num_sms() * 8;
   k_solve_hp<T><<<grid, warps * 32, smem, st>>>(p, all_bins ? 1 : 0, warps);

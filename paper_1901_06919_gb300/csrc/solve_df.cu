@@ -345,7 +345,7 @@ template <int NMAX, int S>
 cudaError_t launch_df_n(const SolveParams& p, bool all_bins, cudaStream_t st) {
   const size_t per_warp = (size_t)(2 * NMAX + NMAX * (NMAX + 1) / 2 + NMAX) * sizeof(float4);
   const size_t smem = per_warp * kDfWarps;
-  cudaError_t e = cudaFuncSetAttribute(k_solve_df<NMAX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem((const void*)k_solve_df<NMAX, S>, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

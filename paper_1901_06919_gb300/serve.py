@@ -1,0 +1,267 @@
+"""Serving: resident FDLs and continuous batching of render / refocus requests.
+
+* ``FdlStore`` keeps fitted FDLs (layer spectra + disparities) on the device under
+  a byte budget; admitting a new light field fits it on a side stream, evicts the
+  least recently used FDLs that no in-flight request reads, and rolls back
+  cleanly if it cannot make room or the allocation fails.
+* ``Server`` groups requests by image size.  Each size class owns two batch
+  buffers, each with its own stream, device descriptor array (``fdl_request``),
+  batch-count word and workspace, and a CUDA graph that copies the descriptors
+  in and runs ``fdl_refocus`` over them.  A tick fills whichever buffer is free
+  with the queued requests (up to its capacity) and replays its graph, so
+  requests that arrive while a batch is on the GPU go into the next batch and
+  the two batches overlap on the device.  Completion is polled with bounded
+  waits (``TimeoutError`` past the deadline).
+"""
+
+from __future__ import annotations
+
+import collections
+import ctypes as ct
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import fdl
+
+
+class AdmissionError(RuntimeError):
+    pass
+
+
+@dataclass
+class FdlEntry:
+    fid: int
+    layers: torch.Tensor
+    d: torch.Tensor
+    H: int
+    W: int
+    C: int
+    N: int
+    nbytes: int
+    refs: int = 0
+    last_used: float = 0.0
+
+
+class FdlStore:
+    """Resident FDLs under a device-memory budget (bytes of layer spectra + disparities)."""
+
+    def __init__(self, budget_bytes: int, device, allocate=None):
+        self.budget = int(budget_bytes)
+        self.device = torch.device(device)
+        self.entries: collections.OrderedDict[int, FdlEntry] = collections.OrderedDict()
+        self._allocate = allocate or (lambda shape, dtype: torch.empty(shape, dtype=dtype, device=self.device))
+
+    @property
+    def bytes_used(self) -> int:
+        return sum(e.nbytes for e in self.entries.values())
+
+    @staticmethod
+    def fdl_bytes(N, C, H, W) -> int:
+        return N * C * H * (W // 2 + 1) * 8 + N * 4
+
+    def _make_room(self, need: int) -> list[int]:
+        """FDLs to evict (least recently used, not in use) so that `need` more bytes fit."""
+        free = self.budget - self.bytes_used
+        victims = []
+        for fid, e in sorted(self.entries.items(), key=lambda kv: kv[1].last_used):
+            if free >= need:
+                break
+            if e.refs == 0:
+                victims.append(fid)
+                free += e.nbytes
+        if free < need:
+            raise AdmissionError(f"cannot fit {need} bytes within the {self.budget}-byte budget")
+        return victims
+
+    def admit(self, fid: int, views: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float = 1e-2,
+              eps: float = 1e-4, stream=None) -> FdlEntry:
+        """Fit and keep an FDL; on any failure nothing changes (already resident FDLs stay)."""
+        if fid in self.entries:
+            raise AdmissionError(f"FDL {fid} is already resident")
+        K, C, H, W = views.shape
+        N = d.numel()
+        need = self.fdl_bytes(N, C, H, W)
+        victims = self._make_room(need)
+        try:
+            layers = self._allocate((N, C, H, W // 2 + 1), torch.complex64)
+            dd = self._allocate((N,), torch.float32)
+        except (RuntimeError, MemoryError) as e:
+            raise AdmissionError(f"allocation failed: {e}") from e
+        dd.copy_(d)
+        if layers.is_cuda:
+            fdl.fit(views, u, dd, lam, eps, out=layers, stream=stream)
+        for v in victims:
+            self.entries.pop(v)
+        e = FdlEntry(fid, layers, dd, H, W, C, N, need, last_used=time.perf_counter())
+        self.entries[fid] = e
+        return e
+
+    def get(self, fid: int) -> FdlEntry:
+        e = self.entries[fid]
+        e.last_used = time.perf_counter()
+        return e
+
+
+@dataclass
+class Request:
+    rid: int
+    fid: int
+    u0: tuple
+    s: float = 0.0
+    aperture: str = "pinhole"
+    radius: float = 0.0
+    t_arrival: float = 0.0
+    t_done: float | None = None
+    out: torch.Tensor | None = None
+    batch_size: int = 0
+
+
+class _Batch:
+    """One batch buffer of a size class: stream, descriptors, count, workspace, graph."""
+
+    def __init__(self, H, W, C, cap, Nmax, device):
+        self.H, self.W, self.C, self.cap, self.Nmax = H, W, C, cap, Nmax
+        self.stream = torch.cuda.Stream(device=device)
+        self.host_desc = torch.zeros(cap * ct.sizeof(L.Request), dtype=torch.uint8).pin_memory()
+        self.host_count = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.dev_desc = torch.zeros(cap * ct.sizeof(L.Request), dtype=torch.uint8, device=device)
+        self.dev_count = torch.zeros(1, dtype=torch.int32, device=device)
+        lib = L.load()
+        self.ws = fdl.workspace(lib.fdl_refocus_workspace_size(cap, C, H, W), device)
+        self.graph = None
+        self.done = torch.cuda.Event()
+        self.requests: list[Request] = []
+        self.busy = False
+
+    def _body(self):
+        self.dev_desc.copy_(self.host_desc, non_blocking=True)
+        self.dev_count.copy_(self.host_count, non_blocking=True)
+        fdl.refocus(self.dev_desc, self.cap, self.C, self.H, self.W, self.Nmax, count=self.dev_count, ws=self.ws)
+
+    def capture(self):
+        # warm up (loads modules, sets kernel attributes) with an empty batch, then capture
+        with torch.cuda.stream(self.stream):
+            self.host_count.zero_()
+            self._body()
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self._body()
+        self.stream.synchronize()
+
+    def launch(self, reqs: list[Request], store: FdlStore, pts: dict):
+        arr = (L.Request * self.cap).from_buffer(self.host_desc.numpy())
+        for i, r in enumerate(reqs):
+            e = store.get(r.fid)
+            p = pts.get(r.aperture)
+            arr[i] = L.Request(e.layers.data_ptr(), e.d.data_ptr(), r.out.data_ptr(),
+                               p.data_ptr() if p is not None else None, e.N, 0 if p is None else p.shape[0],
+                               L.APERTURE[r.aperture], float(r.u0[0]), float(r.u0[1]), float(r.s), float(r.radius), 0)
+            e.refs += 1
+            r.batch_size = len(reqs)
+        self.host_count[0] = len(reqs)
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+            self.done.record(self.stream)
+        self.requests = list(reqs)
+        self.busy = True
+
+
+class Server:
+    """Continuous batching of render / refocus requests over resident FDLs."""
+
+    def __init__(self, store: FdlStore, sizes, Nmax: int = 64, capacity: int = 32, pool: int = 128):
+        self.store = store
+        self.dev = store.device
+        self.classes = {}
+        self.pool = {}
+        for (H, W, C) in sizes:
+            self.classes[(H, W, C)] = [_Batch(H, W, C, capacity, Nmax, self.dev) for _ in range(2)]
+            self.pool[(H, W, C)] = [torch.empty((C, H, W), dtype=torch.float32, device=self.dev) for _ in range(pool)]
+        for bs in self.classes.values():
+            for b in bs:
+                b.capture()
+        self.queue: dict[tuple, collections.deque] = {k: collections.deque() for k in self.classes}
+        self.completed: list[Request] = []
+        self.pts = {}
+
+    def submit(self, r: Request):
+        e = self.store.entries[r.fid]
+        self.queue[(e.H, e.W, e.C)].append(r)
+
+    def release(self, r: Request):
+        """Return a completed request's output buffer to its pool."""
+        e_key = tuple(r.out.shape[1:]) + (r.out.shape[0],)
+        self.pool[e_key].append(r.out)
+        r.out = None
+
+    def _poll(self):
+        now = None
+        for bs in self.classes.values():
+            for b in bs:
+                if b.busy and b.done.query():
+                    now = now or time.perf_counter()
+                    for r in b.requests:
+                        r.t_done = now
+                        self.store.entries[r.fid].refs -= 1
+                        self.completed.append(r)
+                    b.requests = []
+                    b.busy = False
+
+    def tick(self) -> int:
+        """Poll finished batches, then launch queued requests into free buffers; returns launches."""
+        self._poll()
+        launched = 0
+        for key, bs in self.classes.items():
+            q = self.queue[key]
+            for b in bs:
+                if not q:
+                    break
+                if b.busy:
+                    continue
+                n = min(len(q), b.cap, len(self.pool[key]))
+                if n == 0:
+                    break
+                reqs = [q.popleft() for _ in range(n)]
+                for r in reqs:
+                    r.out = self.pool[key].pop()
+                b.launch(reqs, self.store, self.pts)
+                launched += 1
+        return launched
+
+    def drain(self, timeout_s: float = 30.0):
+        """Run ticks until every queued request has completed (bounded wait)."""
+        t0 = time.perf_counter()
+        while any(self.queue.values()) or any(b.busy for bs in self.classes.values() for b in bs):
+            self.tick()
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("requests did not complete within the deadline")
+
+    def run_trace(self, trace: list[Request], timeout_s: float = 120.0, keep_outputs: bool = False):
+        """Replay requests at their arrival times (seconds from the start) in real time."""
+        t0 = time.perf_counter()
+        i = 0
+        trace = sorted(trace, key=lambda r: r.t_arrival)
+        for r in trace:
+            r.t_arrival += t0
+        while i < len(trace) or any(self.queue.values()) or any(b.busy for bs in self.classes.values() for b in bs):
+            now = time.perf_counter()
+            while i < len(trace) and trace[i].t_arrival <= now:
+                self.submit(trace[i])
+                i += 1
+            self.tick()
+            if not keep_outputs:
+                for r in self.completed:
+                    if r.out is not None:
+                        self.release(r)
+            if now - t0 > timeout_s:
+                raise TimeoutError("trace did not complete within the deadline")
+        lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in trace])
+        return {"requests": len(trace), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "wall_s": time.perf_counter() - t0,
+                "mean_batch": float(np.mean([r.batch_size for r in trace]))}
