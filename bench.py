@@ -344,6 +344,218 @@ def time_fp64_path(device, views, u, d, steps=2):
             "render_mpix_s": H * W / float(np.mean(lat)) / 1e3}
 
 
+
+# ------------------------------------------------------------------ serving form
+def serving_leg(device, n_requests=2000, rate=2000.0, budget=40e9, seed=0):
+    """16 resident FDLs (256^2 / 512^2 / 1024^2 RGB, N in {16, 30, 40}, fitted from 7x7-view
+    occluding-plane scenes), Poisson arrivals at `rate`, half view renders (u in [-4,4]^2) and
+    half refocus (disc or square, radius U(0,3), focus U(-3,3)); a new light field is admitted
+    every 500 requests.  Also the same requests all at once (throughput), and the plain FP64
+    path serving them one at a time (measured service times, FIFO queue on the same arrivals)."""
+    import torch
+
+    from paper_1901_06919_gb300.serve import FdlStore, Request, Server
+    from scenes import occluding_planes, view_grid
+
+    rng = np.random.default_rng(seed)
+    sizes = [256, 512, 1024]
+    Ns = [16, 30, 40]
+    u7 = view_grid(3)
+    U = torch.from_numpy(u7).to(device)
+    scenes = {n: torch.from_numpy(occluding_planes(20 + n, n, n, 3, u7)[0]).to(device) for n in sizes}
+    store = FdlStore(int(budget), device)
+    fit_stream = torch.cuda.Stream(device=device)
+    spec_of = {}
+
+    def admit(fid):
+        n = sizes[fid % 3]
+        Nl = Ns[(fid // 3) % 3]
+        d = torch.linspace(-3, 3, Nl, device=device)
+        with torch.cuda.stream(fit_stream):
+            store.admit(fid, scenes[n], U, d, lam=1e-2, stream=fit_stream)
+            ev = torch.cuda.Event()
+            ev.record(fit_stream)
+        spec_of[fid] = (n, Nl, ev)
+
+    t0 = time.perf_counter()
+    for fid in range(16):
+        admit(fid)
+    fit_stream.synchronize()
+    admit_s = time.perf_counter() - t0
+    srv = Server(store, sizes=[(n, n, 3) for n in sizes], Nmax=40, capacity=32, pool=96)
+
+    def make_trace(t_gap):
+        tr = []
+        t = 0.0
+        for i in range(n_requests):
+            t += t_gap(i)
+            view = i % 2 == 0
+            tr.append(Request(i, -1, tuple(rng.uniform(-4, 4, 2)), 0.0 if view else float(rng.uniform(-3, 3)),
+                              "pinhole" if view else ("disc" if rng.random() < 0.5 else "square"),
+                              0.0 if view else float(rng.uniform(0, 3)), t_arrival=t))
+        return tr
+
+    def run(trace):
+        next_fid = [max(store.entries) + 1]
+        picks = rng.integers(0, 1 << 30, len(trace))
+
+        orig_submit = srv.submit
+
+        def submit(r):
+            live = [f for f in store.entries if spec_of[f][2].query()]
+            r.fid = live[int(picks[r.rid]) % len(live)]
+            if r.rid > 0 and r.rid % 500 == 0:
+                admit(next_fid[0])
+                next_fid[0] += 1
+            orig_submit(r)
+
+        srv.submit = submit
+        try:
+            st = srv.run_trace(trace)
+        finally:
+            srv.submit = orig_submit
+        return st
+
+    poisson = make_trace(lambda i: float(rng.exponential(1.0 / rate)))
+    # warm-up burst, then the timed Poisson trace and a saturation trace
+    run(make_trace(lambda i: 0.0)[:64])
+    st = run(poisson)
+    pix = sum(spec_of[r.fid][0] ** 2 for r in poisson)
+    st["mpix_s"] = pix / st["wall_s"] / 1e6
+    sat = make_trace(lambda i: 0.0)
+    st_sat = run(sat)
+    pix_sat = sum(spec_of[r.fid][0] ** 2 for r in sat)
+    st_sat["mpix_s"] = pix_sat / st_sat["wall_s"] / 1e6
+    out = {"poisson": st, "saturation": st_sat, "fdls_resident": len(store.entries),
+           "fdl_bytes": store.bytes_used, "admit16_s": admit_s}
+    # the plain FP64 path, one request at a time: measured service times per size, FIFO queue
+    svc = {}
+    for n in sizes:
+        fid = next(f for f in store.entries if spec_of[f][0] == n)
+        e = store.entries[fid]
+        p = Fp64Render(device, e.layers, e.d)
+        times = []
+        for k in range(8):
+            t = time.perf_counter()
+            p.render(tuple(rng.uniform(-4, 4, 2)), float(rng.uniform(-3, 3)), float(rng.uniform(0, 3)) * (k % 2))
+            times.append(time.perf_counter() - t)
+        svc[n] = float(np.median(times[2:]))
+        del p
+    torch.cuda.empty_cache()
+    arr = np.array([r.t_arrival - poisson[0].t_arrival for r in poisson])
+    busy = 0.0
+    lat = []
+    for r, a in zip(poisson, arr):
+        start = max(a, busy)
+        busy = start + svc[spec_of[r.fid][0]]
+        lat.append((busy - a) * 1e3)
+    out["fp64_one_at_a_time"] = {"service_ms": {str(k): v * 1e3 for k, v in svc.items()},
+                                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                 "mpix_s": pix / busy / 1e6}
+    return out
+
+
+class Fp64Render:
+    """One image of Eq. BsFourier with torch complex128 ops (the plain FP64 path)."""
+
+    def __init__(self, device, layers, d):
+        import torch
+
+        self.torch = torch
+        self.X = layers.to(torch.complex128)
+        self.d = d.double()
+        Nl, Cl, Hh, Wh = layers.shape
+        self.H, self.W = Hh, 2 * (Wh - 1)
+        ky = torch.fft.fftfreq(Hh, device=device, dtype=torch.float64)
+        kx = torch.arange(Wh, device=device, dtype=torch.float64) / self.W
+        self.wy, self.wx = torch.meshgrid(ky, kx, indexing="ij")
+
+    def render(self, u0, s=0.0, radius=0.0):
+        torch = self.torch
+        ph = 2 * torch.pi * self.d[:, None, None] * (u0[0] * self.wx + u0[1] * self.wy)[None]
+        coef = torch.polar(torch.ones((), dtype=torch.float64, device=self.X.device), ph)
+        if radius > 0:
+            z = 2 * torch.pi * radius * ((s - self.d)[:, None, None] * torch.sqrt(self.wx ** 2 + self.wy ** 2)[None]).abs()
+            safe = torch.where(z == 0, torch.ones_like(z), z)
+            coef = coef * torch.where(z == 0, torch.ones_like(z), 2 * torch.special.bessel_j1(safe) / safe)
+        img = torch.fft.irfft2((coef[:, None] * self.X).sum(0), s=(self.H, self.W))
+        torch.cuda.synchronize()
+        return img
+
+
+# ------------------------------------------------------------------ precision form
+def precision_leg(device, lams=(1e-3, 1e-2, 1e-1), nb=24):
+    """7x7 views, 1024x1024 RGB, N=40 on linspace(-4, 4): fit time and layer error per lambda
+    against the FP64 oracle on a sample of frequencies (low ones, where conditioning is worst,
+    and random ones; the oracle's inputs come from its own direct DFT of the views)."""
+    import torch
+
+    import paper_1901_06919_gb300 as F
+    from oracle import fdl_oracle as O
+    from scenes import occluding_planes, view_grid
+
+    u = view_grid(3)
+    d = np.linspace(-4, 4, 40).astype(np.float32)
+    n = 1024
+    views, _ = occluding_planes(7, n, n, 3, u)
+    V, U, D = (torch.from_numpy(a).to(device) for a in (views, u, d))
+    rng = np.random.default_rng(2)
+    ky = np.concatenate([[0, 1, 0, 2, 1023], rng.integers(0, n, nb - 5)])
+    kx = np.concatenate([[1, 0, 2, 1, 3], rng.integers(0, n // 2 + 1, nb - 5)])
+    b = O.dft_at_bins(views.astype(np.float64), ky, kx)
+    out = {}
+    for lam in lams:
+        x, ws = F.fit(V, U, D, lam)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        F.fit(V, U, D, lam, out=x, ws=ws)
+        e.record()
+        torch.cuda.synchronize()
+        ref = np.moveaxis(O.solve_bins(np.moveaxis(b, -1, 0), u, d.astype(np.float64), O.freq_y(n)[ky], kx / n,
+                                       lam, 1e-4), 0, -1)
+        got = x.cpu().numpy()[:, :, ky, kx]
+        out[str(lam)] = {"fit_ms": a.elapsed_time(e), "fit_mfreq_s": n * (n // 2 + 1) / a.elapsed_time(e) / 1e3,
+                         "layer_rel_l2_sampled": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                         "tiers": ws.tier_counts()}
+    return out
+
+
+# ------------------------------------------------------------------ differentiation form
+def calib_leg(device, steps=200):
+    """5x5 views jittered by U(+-0.15), 256x256 gray, 12 true disparities U(-2, 2); 200 Adam
+    steps from the grid and linspace(-2, 2, 12) on 4096-frequency subsets."""
+    import torch
+
+    import paper_1901_06919_gb300 as F
+    from paper_1901_06919_gb300.calib import calibrate
+    from scenes import layered_scene, view_grid
+
+    rng = np.random.default_rng(0)
+    u_true = view_grid(2).astype(np.float64) + rng.uniform(-0.15, 0.15, (25, 2))
+    d_true = np.sort(rng.uniform(-2, 2, 12))
+    views, _ = layered_scene(1, 256, 256, 1, u_true.astype(np.float32), d_true.astype(np.float32), sigma=0.0)
+    S = F.rfft2(torch.from_numpy(views).to(device))
+    u0 = torch.from_numpy(view_grid(2)).to(device)
+    d0 = torch.linspace(-2, 2, 12, device=device)
+    calibrate(S, u0, d0, steps=3)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = calibrate(S, u0, d0, steps=steps, lr=1e-2, subset=4096)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    a = res.u.cpu().numpy().astype(np.float64)
+    a -= a.mean(0)
+    tt = u_true - u_true.mean(0)
+    c = (a * tt).sum() / (a * a).sum()
+    g = view_grid(2).astype(np.float64)
+    g -= g.mean(0)
+    c0 = (g * tt).sum() / (g * g).sum()
+    return {"steps": steps, "steps_per_s": steps / dt, "loss_first": res.losses[0], "loss_last": res.losses[-1],
+            "u_rms_err_init": float(np.sqrt(((c0 * g - tt) ** 2).mean())),
+            "u_rms_err_final": float(np.sqrt(((c * a - tt) ** 2).mean()))}
+
 # ------------------------------------------------------------------ oracle on the host
 def oracle_sample_step(views, u, d, s_list, n_img=24, n_bins=4096, n_render=4):
     """Bounded sample of one step run by the FP64 oracle; returns the full-step time estimate (s)."""
@@ -431,6 +643,9 @@ def main():
     ap.add_argument("--impl", default="fdl", choices=["fdl", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the torch FP64 comparator leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-precision", action="store_true", help="skip the 1024x1024 precision leg")
+    ap.add_argument("--no-calib", action="store_true", help="skip the calibration leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
@@ -502,6 +717,18 @@ def main():
             line["fp64_gpu_path"] = time_fp64_path(device, views, u, d)
         except Exception as e:  # reported, not hidden
             line["fp64_gpu_path"] = {"error": repr(e)[:200]}
+    if rank == 0 and not args.no_serve:
+        del path
+        torch.cuda.empty_cache()
+        line["serving"] = serving_leg(device)
+        line["latency"]["serving_p50_ms"] = line["serving"]["poisson"]["p50_ms"]
+        line["latency"]["serving_p99_ms"] = line["serving"]["poisson"]["p99_ms"]
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_precision:
+        line["precision"] = precision_leg(device)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_calib:
+        line["calibration"] = calib_leg(device)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(views, u, d, s_list)
     if rank == 0:
@@ -510,19 +737,31 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def df_ops_per_frequency(K, N, C):
+    """FP32 operations of the double-float solve at one frequency, counted from its formulas:
+    compensated Gram update 54 per off-diagonal entry and view, double-float exp 198 per
+    (view, layer), right-hand side 52 per (view, layer, channel), Cholesky update 52 per
+    (r, l, k) plus 60 per pivot and 14 per scaled entry, triangular solves 52 per entry and
+    channel in each direction."""
+    gram = (N * (N - 1) // 2) * K * 54
+    exps = N * K * 198
+    rhs = N * K * C * 52
+    chol = ((N ** 3 - N) // 6) * 52 + N * 60 + (N * (N - 1) // 2) * 14
+    solves = 2 * (N * (N - 1) // 2) * C * 52 + 2 * N * C * 14
+    return gram + exps + rhs + chol + solves
+
+
 def roofline_entry(legs, clk):
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    hbm = None
-    if os.path.exists(peaks_path):
-        hbm = json.load(open(peaks_path)).get("hbm_gbs")
-    # placeholder until the launch list names the dominant kernel: the DFT of the views (HBM bound),
-    # algorithmic bytes = views read + half spectra written
-    bytes_alg = 243 * H * W * 4 + 243 * H * (W // 2 + 1) * 8
-    ach = bytes_alg / (legs["rfft2_ms"] / 1e3) / 1e9
-    peak = hbm or 6800.0
-    return {"kernel": "rfft2 (row + column pass)", "bound": "hbm", "achieved": ach, "peak": peak,
-            "unit": "GB/s", "frac": ach / peak, "traffic": None,
-            "peak_source": "measured" if hbm else "fallback"}
+    """The dominant kernel is the double-float solve (launch list); it is bound by the FP32 pipe."""
+    ops = df_ops_per_frequency(81, N, C) * q_half()
+    ms = legs["solve_df_all_ms"]
+    achieved = ops / (ms / 1e3) / 1e12
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = 152 * 128 * mhz * 1e6 / 1e12  # one FP32 operation per lane per cycle
+    return {"kernel": "k_solve_df (double-float per-frequency solve, all 131,584 frequencies)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFP32op/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock sampled in the run)",
+            "work_per_frequency_fp32_ops": df_ops_per_frequency(81, N, C)}
 
 
 if __name__ == "__main__":

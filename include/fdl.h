@@ -67,7 +67,9 @@ extern "C" {
 /* ---- arithmetic of the per-frequency solve ----------------------------- */
 #define FDL_PREC_MIXED 0 /* FP32 where the estimated condition number of
                             A*A + lambda Gamma*Gamma is below kappa_max;
-                            double-float (FP32 pairs, ~2^-48) elsewhere     */
+                            double-float (FP32 pairs, ~2^-48) elsewhere,
+                            except the frequencies that native FP64 must
+                            take to meet df_error_budget                      */
 #define FDL_PREC_DF 1    /* double-float at every frequency                   */
 #define FDL_PREC_F64 2   /* native FP64 at every frequency                    */
 #define FDL_PREC_F32 3   /* FP32 at every frequency, no certification         */
@@ -86,6 +88,13 @@ typedef struct fdl_fit_opts {
   int precision;    /* FDL_PREC_*                                                  */
   double kappa_max; /* FDL_PREC_MIXED: largest estimated condition number kept in
                        FP32 (<= 0 selects the default, 100)                        */
+  double df_error_budget; /* FDL_PREC_MIXED: estimated relative L2 error that the
+                             double-float frequencies may leave in the layers; the
+                             frequencies with the largest estimated errors (condition
+                             estimate x solution norm), and any whose double-float
+                             factorisation breaks down, are re-solved in native FP64
+                             until the estimate of the rest is within it
+                             (<= 0 selects the default, 4e-6; N <= 48 only)        */
 } fdl_fit_opts;
 
 /* One image to render (Eq. BsFourier): the FDL it reads, the viewpoint u0,
@@ -145,7 +154,7 @@ FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W,
  * and hosts (plugins, renderers, frameworks with their own caching allocator)
  * that own the whole device-memory budget and forbid allocations by libraries.
  * The paper has no counterpart: this is an integration variant only.
- * Its scratch is a fixed array inside the library (2,117,888 bytes on every
+ * Its scratch is a fixed array inside the library (8,454,400 bytes on every
  * GPU that loads it, held until the process exits); H * (W/2 + 1) must not
  * exceed 525,312 (a 1024 x 1024 image), otherwise FDL_ENOMEM.  The first call
  * on each device looks up the array's device address, so make it before any
@@ -158,10 +167,10 @@ FDL_API int fdl_fit_spectra_noalloc(const float* spectra, int K, int C, int H, i
                                     void* stream);
 
 /* After fdl_fit / fdl_fit_spectra on `stream`: counts[0] = frequencies solved
- * in FP32, counts[1] = frequencies solved in double-float or FP64, counts[2]
- * = frequencies whose high-precision factorisation broke down (left as
- * zeros), counts[3] = frequencies with non-finite input.  counts is a HOST
- * int[4]; this call synchronises `stream`. */
+ * in FP32, counts[1] = in double-float, counts[2] = in native FP64,
+ * counts[3] = frequencies whose last factorisation broke down (left as
+ * zeros), counts[4] = frequencies with non-finite input.  counts is a HOST
+ * int[5]; this call synchronises `stream`. */
 FDL_API int fdl_fit_tier_counts(const void* workspace, int* counts, void* stream);
 
 /* ---- rendering (Sec. VI-A, Eq. FourierView / Eq. BsFourier) ----------- */

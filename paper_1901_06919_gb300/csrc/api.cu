@@ -12,6 +12,10 @@ using namespace fdl;
 namespace {
 
 constexpr size_t kAlign = 256;
+// Error of the double-float solve per unit of (condition estimate x solution norm).
+// Measured: the bound kappa |x| 2^-47 overstates the error of the 7x7-view, 40-layer
+// solve about tenfold, so the estimate uses a tenth of 2^-47.
+constexpr double kDfUnit = 7.1e-16;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -37,7 +41,12 @@ struct Carver {
 struct FitWs {
   int* counters;
   float4* exp_table;
+  float4* fft_tables;
   int* flagged;
+  int* flagged64;
+  float* err;
+  float* xn2;
+  void* select;
   float2* spec_main;
   float2* spec_nyq;
   size_t bytes;
@@ -48,7 +57,12 @@ FitWs carve_fit(void* ws, int K, int C, int H, int W, bool with_spectra) {
   FitWs f;
   f.counters = cv.take<int>(16);
   f.exp_table = cv.take<float4>(1024);
+  f.fft_tables = cv.take<float4>((size_t)H + W);
   f.flagged = cv.take<int>((size_t)H * (W / 2 + 1));
+  f.flagged64 = cv.take<int>((size_t)H * (W / 2 + 1));
+  f.err = cv.take<float>((size_t)H * (W / 2 + 1));
+  f.xn2 = cv.take<float>((size_t)H * (W / 2 + 1));
+  f.select = cv.take<char>(select_scratch_bytes());
   if (with_spectra) {
     f.spec_main = cv.take<float2>((size_t)K * C * H * (W / 2));
     f.spec_nyq = cv.take<float2>((size_t)K * C * H);
@@ -67,6 +81,7 @@ int check_fit_args(int K, int C, int H, int W, int N, const fdl_fit_opts* o) {
   if (o->reg < FDL_REG_VIEW2 || o->reg > FDL_REG_L2) return FDL_EINVAL;
   if (o->precision < FDL_PREC_MIXED || o->precision > FDL_PREC_F32) return FDL_EINVAL;
   if (o->precision == FDL_PREC_F32 && N > 32) return FDL_ENOTSUP;
+  if (std::isnan(o->kappa_max) || std::isnan(o->df_error_budget)) return FDL_EINVAL;
   return FDL_OK;
 }
 
@@ -89,32 +104,52 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
   p.lam_eps_d = o->lambda * (o->reg == FDL_REG_VIEW2 ? o->eps : 0.0);
   p.kappa_max = (float)(o->kappa_max > 0.0 ? o->kappa_max : 100.0);
   p.flagged = f.flagged;
+  p.flagged64 = f.flagged64;
+  p.err = nullptr;
+  p.xn2 = nullptr;
+  const double budget = o->df_error_budget > 0.0 ? o->df_error_budget : 4e-6;
   p.counters = f.counters;
   p.exp_table = f.exp_table;
   cudaError_t e = cudaMemsetAsync(f.counters, 0, 16 * sizeof(int), st);
   if (e != cudaSuccess) return FDL_ECUDA;
   e = launch_exp_table(f.exp_table, st);
   if (e != cudaSuccess) return FDL_ECUDA;
-  // double-float: registers for N <= 48, shared memory beyond
-  auto solve_df = [&](bool all_bins) {
-    return solve_df_supported(N) ? launch_solve_df(p, all_bins, st) : launch_solve_hp(p, all_bins, false, st);
+  // double-float: registers for N <= 48, shared memory beyond.  With the FP64 tier the
+  // double-float pass records an error scale per frequency; those with the largest
+  // estimated errors are then re-solved in native FP64 until the estimated error of the
+  // rest is within `budget` (relative L2 of the layers).
+  const int Qs = H * (W / 2 + 1);
+  auto solve_df = [&](bool all_bins, bool fp64_tier) {
+    if (!solve_df_supported(N)) return launch_solve_hp(p, all_bins, false, 0, st);
+    cudaError_t r = cudaSuccess;
+    if (fp64_tier) {
+      p.err = f.err;
+      p.xn2 = f.xn2;
+      r = cudaMemsetAsync(f.err, 0, (size_t)Qs * sizeof(float), st);
+      if (r == cudaSuccess) r = cudaMemsetAsync(f.xn2, 0, (size_t)Qs * sizeof(float), st);
+    }
+    if (r == cudaSuccess) r = launch_solve_df(p, all_bins, st);
+    if (r == cudaSuccess && fp64_tier)
+      r = launch_select_fp64(f.err, f.xn2, Qs, kDfUnit, budget, f.select, f.flagged64, f.counters + 5, st);
+    if (r == cudaSuccess && fp64_tier) r = launch_solve_hp(p, false, true, 1, st);
+    return r;
   };
   switch (o->precision) {
     case FDL_PREC_F32:
       e = launch_solve_f32(p, false, st);
       break;
     case FDL_PREC_DF:
-      e = solve_df(true);
+      e = solve_df(true, false);
       break;
     case FDL_PREC_F64:
-      e = launch_solve_hp(p, true, true, st);
+      e = launch_solve_hp(p, true, true, 0, st);
       break;
     default:
       if (N > 32) {
-        e = solve_df(true);
+        e = solve_df(true, true);
       } else {
         e = launch_solve_f32(p, true, st);
-        if (e == cudaSuccess) e = solve_df(false);
+        if (e == cudaSuccess) e = solve_df(false, true);
       }
   }
   return cuda_status(e);
@@ -158,7 +193,7 @@ FDL_API int fdl_version(void) { return 1; }
 // ------------------------------------------------------------------ DFTs
 FDL_API size_t fdl_rfft2_workspace_size(int nimg, int H, int W) {
   if (nimg < 1 || !shape_ok(H, W)) return 0;
-  return spec_tmp_bytes(nimg, H, W);
+  return spec_tmp_bytes(nimg, H, W) + align_up(fft_df_table_bytes(H, W));
 }
 
 FDL_API int fdl_rfft2(const float* images, int nimg, int H, int W, float* spectra, void* workspace,
@@ -167,10 +202,12 @@ FDL_API int fdl_rfft2(const float* images, int nimg, int H, int W, float* spectr
   if (workspace_bytes < fdl_rfft2_workspace_size(nimg, H, W)) return FDL_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float2* tmp = static_cast<float2*>(workspace);
-  cudaError_t e = launch_rfft_rows(images, tmp, (long long)nimg * H, W, st);
+  float4* tables = reinterpret_cast<float4*>(static_cast<char*>(workspace) + spec_tmp_bytes(nimg, H, W));
+  cudaError_t e = launch_twiddle_tables(tables, H, W, st);
+  if (e == cudaSuccess) e = launch_rfft_rows_df(images, tmp, (long long)nimg * H, W, tables, st);
   if (e == cudaSuccess)
-    e = launch_fft_cols_fwd(spec_split(tmp, nullptr, H, W), spec_dense(reinterpret_cast<float2*>(spectra), H, W),
-                            nimg, H, W, st);
+    e = launch_fft_cols_fwd_df(spec_split(tmp, nullptr, H, W), spec_dense(reinterpret_cast<float2*>(spectra), H, W),
+                               nimg, H, W, tables, st);
   return cuda_status(e);
 }
 
@@ -208,9 +245,10 @@ FDL_API int fdl_fit(const float* views, int K, int C, int H, int W, const float*
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   FitWs f = carve_fit(workspace, K, C, H, W, true);
   const int nimg = K * C;
-  cudaError_t e = launch_rfft_rows(views, f.spec_main, (long long)nimg * H, W, st);
+  cudaError_t e = launch_twiddle_tables(f.fft_tables, H, W, st);
+  if (e == cudaSuccess) e = launch_rfft_rows_df(views, f.spec_main, (long long)nimg * H, W, f.fft_tables, st);
   SpecView b = spec_split(f.spec_main, f.spec_nyq, H, W);
-  if (e == cudaSuccess) e = launch_fft_cols_fwd(b, b, nimg, H, W, st);
+  if (e == cudaSuccess) e = launch_fft_cols_fwd_df(b, b, nimg, H, W, f.fft_tables, st);
   if (e != cudaSuccess) return FDL_ECUDA;
   return run_solve(b, K, C, H, W, u, d, N, opts, layers, f, st);
 }
@@ -236,11 +274,15 @@ FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W, co
 FDL_API int fdl_fit_tier_counts(const void* workspace, int* counts, void* stream) {
   if (!workspace || !counts) return FDL_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int tmp[4];
+  int tmp[7];
   cudaError_t e = cudaMemcpyAsync(tmp, workspace, sizeof(tmp), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return FDL_ECUDA;
-  std::memcpy(counts, tmp, sizeof(tmp));
+  counts[0] = tmp[0];  // FP32
+  counts[1] = tmp[1];  // double-float
+  counts[2] = tmp[6];  // native FP64
+  counts[3] = tmp[2];  // breakdowns
+  counts[4] = tmp[3];  // non-finite inputs
   return FDL_OK;
 }
 
@@ -341,13 +383,15 @@ FDL_API int fdl_calib_grad(const float* spectra, int K, int C, int H, int W, con
 // ------------------------------------------------------------------ fixed-scratch fit
 // Scratch of fdl_fit_spectra_noalloc: a file-scope device array, so that the
 // entry point never allocates.  Every GPU that loads the library holds it
-// (2,117,888 bytes) until the process exits; all calls on a device share it.
+// (8,454,400 bytes) until the process exits; all calls on a device share it.
 namespace {
 
 constexpr size_t kNoAllocMaxBins = 1024 * 513;  // H * (W/2 + 1) of a 1024 x 1024 image
 constexpr size_t kNoAllocCounters = 256;
 constexpr size_t kNoAllocTable = 1024 * sizeof(float4);
-constexpr size_t kNoAllocBytes = kNoAllocCounters + kNoAllocTable + kNoAllocMaxBins * sizeof(int);
+constexpr size_t kNoAllocSelect = 32768;  // >= select_scratch_bytes()
+constexpr size_t kNoAllocBytes =
+    kNoAllocCounters + kNoAllocTable + kNoAllocSelect + 4 * kNoAllocMaxBins * sizeof(int);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -380,6 +424,7 @@ extern "C" FDL_API int fdl_fit_spectra_noalloc(const float* spectra, int K, int 
   if (s != FDL_OK) return s;
   if (!spectra || !u || !d || !layers) return FDL_EINVAL;
   if ((size_t)H * (W / 2 + 1) > kNoAllocMaxBins) return FDL_ENOMEM;
+  if (select_scratch_bytes() > kNoAllocSelect) return FDL_ENOTSUP;
   void* base = nullptr;
   s = noalloc_scratch(&base);
   if (s != FDL_OK) return s;
@@ -387,7 +432,12 @@ extern "C" FDL_API int fdl_fit_spectra_noalloc(const float* spectra, int K, int 
   FitWs f;
   f.counters = reinterpret_cast<int*>(b);
   f.exp_table = reinterpret_cast<float4*>(b + kNoAllocCounters);
-  f.flagged = reinterpret_cast<int*>(b + kNoAllocCounters + kNoAllocTable);
+  f.select = b + kNoAllocCounters + kNoAllocTable;
+  f.flagged = reinterpret_cast<int*>(b + kNoAllocCounters + kNoAllocTable + kNoAllocSelect);
+  f.flagged64 = f.flagged + kNoAllocMaxBins;
+  f.err = reinterpret_cast<float*>(f.flagged64 + kNoAllocMaxBins);
+  f.xn2 = f.err + kNoAllocMaxBins;
+  f.fft_tables = nullptr;
   f.spec_main = f.spec_nyq = nullptr;
   f.bytes = kNoAllocBytes;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

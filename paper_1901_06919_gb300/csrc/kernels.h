@@ -26,6 +26,15 @@ cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int 
 // count (nullable, device): only images [0, *count * C) are transformed.
 cudaError_t launch_fft_cols_inv(SpecView in, float2* out, int nimg, int H, int W, const int* count, int C,
                                 cudaStream_t st);
+// The same forward passes with double-float arithmetic inside each pass
+// (fft_df.cu); `tables` = double-float twiddles of lengths W then H, built by
+// launch_twiddle_tables into fft_df_table_bytes(H, W) of workspace.
+size_t fft_df_table_bytes(int H, int W);
+cudaError_t launch_twiddle_tables(float4* tables, int H, int W, cudaStream_t st);
+cudaError_t launch_rfft_rows_df(const float* in, float2* out, long long nrows, int W, const float4* tables,
+                                cudaStream_t st);
+cudaError_t launch_fft_cols_fwd_df(SpecView in, SpecView out, int nimg, int H, int W, const float4* tables,
+                                   cudaStream_t st);
 // Row pass of the inverse real DFT: packed rows (pitch W/2) -> W floats, times scale.
 // req (nullable, device): image b*C + c goes to req[b].out + c*H*W instead of
 // the contiguous `out`; count (nullable, device) limits the images to *count * C.
@@ -42,20 +51,32 @@ struct SolveParams {
   int reg;
   float lam, lam_eps;  // lambda and lambda*eps
   double lam_d, lam_eps_d;
-  float kappa_max;
-  int* flagged;        // list of bins for the high-precision pass
-  int* counters;       // [0] fp32 bins, [1] high-precision bins, [2] breakdowns, [3] non-finite, [4] list length
+  float kappa_max;     // largest estimated condition number kept in FP32
+  int* flagged;        // bins for the double-float pass (written by the FP32 kernel)
+  int* flagged64;      // bins for the native FP64 pass (chosen from err / xn2)
+  float* err;          // per bin: condition estimate x |x| of the double-float solve (nullable)
+  float* xn2;          // per bin: |x|^2 of the double-float solve
+  int* counters;       // [0] FP32 bins, [1] double-float bins, [2] breakdowns, [3] non-finite,
+                       // [4] double-float list length, [5] FP64 list length, [6] FP64 bins
   const float4* exp_table;  // df table of exp(2 pi i n / 1024), n in [0, 1024)
 };
 cudaError_t launch_solve_f32(const SolveParams& p, bool certify, cudaStream_t st);
-// Solves the bins listed in p.flagged (count in p.counters[4]) or, when
-// all_bins, every stored bin; T = native FP64 when f64 else double-float.
-cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, cudaStream_t st);
+// Solves the bins of list `list` (0: p.flagged / counters[4], 1: p.flagged64 /
+// counters[5]) or, when all_bins, every stored bin; T = native FP64 when f64
+// else double-float (shared-memory matrix, any N <= 64).
+cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, int list, cudaStream_t st);
 cudaError_t launch_exp_table(float4* table, cudaStream_t st);
 // Double-float solve with the matrix in registers (N <= 48); same contract as
 // launch_solve_hp with f64 = false.
 bool solve_df_supported(int N);
 cudaError_t launch_solve_df(const SolveParams& p, bool all_bins, cudaStream_t st);
+
+// ---- FP64 selection (select.cu) ---------------------------------------------
+// Appends to `list` the frequencies with the largest err so that the rest keep
+// u * sqrt(sum err^2) <= budget * sqrt(sum xn2); scratch of select_scratch_bytes().
+size_t select_scratch_bytes();
+cudaError_t launch_select_fp64(const float* err, const float* xn2, int n, double u, double budget, void* scratch,
+                               int* list, int* count, cudaStream_t st);
 
 // ---- render (render.cu) -----------------------------------------------------
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W,

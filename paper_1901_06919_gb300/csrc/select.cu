@@ -1,0 +1,114 @@
+// Choice of the frequencies re-solved in native FP64.
+//
+// The double-float solve records, per frequency q, an error scale
+// e_q = kappa_q |x_q| (condition estimate times solution norm; 0 for
+// frequencies solved elsewhere, +inf where its factorisation broke down) and
+// |x_q|^2.  With u the double-float unit of the solve, the
+// estimated error of the layers is sqrt(sum (u e_q)^2).  These kernels pick
+// the smallest set of largest e_q whose removal brings the estimate of the
+// rest under budget * |X|:
+//   k_err_hist     histogram of log2 e_q: count and sum of e_q^2 per bucket;
+//   k_err_thresh   one thread scans the buckets from the top down;
+//   k_err_compact  appends every frequency at or above the threshold.
+#include "kernels.h"
+
+namespace fdl {
+
+namespace {
+
+// eight buckets per octave: bucket b holds e in [2^((b-1024)/8), 2^((b-1023)/8));
+// the last bucket also holds +inf (factorisations that broke down)
+constexpr int kBuckets = 2048;
+constexpr int kPerOctave = 8;
+
+__device__ __forceinline__ int bucket_of(float e) {
+  if (!(e > 0.f)) return -1;
+  if (isinf(e) || isnan(e)) return kBuckets - 1;
+  const int b = (int)floorf(log2f(e) * kPerOctave) + kBuckets / 2;
+  return b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
+}
+
+__global__ void __launch_bounds__(512) k_err_hist(const float* __restrict__ err, const float* __restrict__ xn2, int n,
+                           double* __restrict__ hist_sq, unsigned int* __restrict__ hist_n, double* __restrict__ xnorm2) {
+  __shared__ double sq[kBuckets];
+  __shared__ unsigned int cnt[kBuckets];
+  __shared__ double xs;
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) {
+    sq[i] = 0.0;
+    cnt[i] = 0;
+  }
+  if (threadIdx.x == 0) xs = 0.0;
+  __syncthreads();
+  double xl = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const float e = err[q];
+    const int b = bucket_of(e);
+    if (b >= 0) {
+      atomicAdd(&cnt[b], 1u);
+      if (isfinite(e)) atomicAdd(&sq[b], (double)e * (double)e);
+    }
+    const float x2 = xn2[q];
+    if (isfinite(x2)) xl += (double)x2;
+  }
+  for (int o = 16; o > 0; o >>= 1) xl += __shfl_xor_sync(0xffffffffu, xl, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&xs, xl);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) {
+    if (cnt[i]) {
+      atomicAdd(&hist_n[i], cnt[i]);
+      atomicAdd(&hist_sq[i], sq[i]);
+    }
+  }
+  if (threadIdx.x == 0) atomicAdd(xnorm2, xs);
+}
+
+// threshold: smallest e such that frequencies with e_q >= threshold go to FP64 and
+// u^2 * sum_{e_q < threshold} e_q^2 <= (budget^2) * sum |x|^2
+__global__ void k_err_thresh(const double* __restrict__ hist_sq, const unsigned int* __restrict__ hist_n,
+                             const double* __restrict__ xnorm2, double u, double budget, float* __restrict__ thresh) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double below = 0.0;
+  for (int b = 0; b < kBuckets - 1; ++b) below += hist_sq[b];
+  const double allow = budget * budget * xnorm2[0] / (u * u);
+  int cut = kBuckets - 1;  // bucket index from which everything goes to FP64 (+inf always)
+  while (cut > 0 && below > allow) {
+    --cut;
+    below -= hist_sq[cut];
+  }
+  thresh[0] = exp2f((float)(cut - kBuckets / 2) / kPerOctave);
+  if (cut == kBuckets - 1) thresh[0] = INFINITY;  // only breakdowns
+}
+
+__global__ void k_err_compact(const float* __restrict__ err, int n, const float* __restrict__ thresh,
+                              int* __restrict__ list, int* __restrict__ count) {
+  const float t = thresh[0];
+  const int tb = isinf(t) ? kBuckets - 1 : (int)floorf(log2f(t) * kPerOctave) + kBuckets / 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int b = bucket_of(err[q]);
+    if (b >= 0 && b >= tb) list[atomicAdd(count, 1)] = q;
+  }
+}
+
+}  // namespace
+
+size_t select_scratch_bytes() { return kBuckets * (sizeof(double) + sizeof(unsigned int)) + 64; }
+
+cudaError_t launch_select_fp64(const float* err, const float* xn2, int n, double u, double budget, void* scratch,
+                               int* list, int* count, cudaStream_t st) {
+  double* hist_sq = static_cast<double*>(scratch);
+  unsigned int* hist_n = reinterpret_cast<unsigned int*>(hist_sq + kBuckets);
+  double* xnorm2 = reinterpret_cast<double*>(hist_n + kBuckets);
+  float* thresh = reinterpret_cast<float*>(xnorm2 + 1);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, select_scratch_bytes(), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = sms * 2;
+  k_err_hist<<<grid, 512, 0, st>>>(err, xn2, n, hist_sq, hist_n, xnorm2);
+  k_err_thresh<<<1, 32, 0, st>>>(hist_sq, hist_n, xnorm2, u, budget, thresh);
+  k_err_compact<<<grid, 512, 0, st>>>(err, n, thresh, list, count);
+  return cudaGetLastError();
+}
+
+}  // namespace fdl

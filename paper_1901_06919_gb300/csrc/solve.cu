@@ -245,8 +245,11 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
 }
 
 // --------------------------------------------------------- high precision
+__device__ __forceinline__ bool r_is_native(R64) { return true; }
+__device__ __forceinline__ bool r_is_native(Rdf) { return false; }
+
 template <class T>
-__global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, int warps) {
+__global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, int warps, int list) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -268,10 +271,11 @@ __global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, 
   cx<T>* G = reinterpret_cast<cx<T>*>(smem4) + warp * hp_warp_elems<T>(N, C);
   cx<T>* Arow = G + N * (N + 1);
   cx<T>* Y = Arow + N;
-  const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(sp.counters + 4));
+  const int* lst = list == 0 ? sp.flagged : sp.flagged64;
+  const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(sp.counters + (list == 0 ? 4 : 5)));
   int nhp = 0, nbad = 0;
   for (int li = blockIdx.x * warps + warp; li < total; li += gridDim.x * warps) {
-    const int q = all_bins ? li : sp.flagged[li];
+    const int q = all_bins ? li : lst[li];
     int ky, kx;
     bin_coords(q, p.H, M, ky, kx);
     const bool ok = hp_solve_bin<T>(p, ky, kx, G, Arow, Y);
@@ -290,7 +294,9 @@ __global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, 
     __syncwarp();
   }
   if (lane == 0) {
-    if (nhp) atomicAdd(sp.counters + 1, nhp);
+    if (nhp) atomicAdd(sp.counters + (r_is_native(T{}) ? 6 : 1), nhp);
+    // a frequency re-solved from the FP64 list was counted by the double-float pass
+    if (nhp && list == 1) atomicSub(sp.counters + 1, nhp);
     if (nbad) atomicAdd(sp.counters + 2, nbad);
   }
 }
@@ -322,15 +328,14 @@ cudaError_t launch_f32_n(const SolveParams& p, bool certify, cudaStream_t st) {
                                kTileBins * NMAX * (NMAX + 1)) * sizeof(float2);
   cudaError_t e = set_smem((const void*)k_solve_f32<NMAX>, smem);
   if (e != cudaSuccess) return e;
+  // one tile per CTA: short CTAs let higher-priority work interleave
   const int ntiles = p.H * (p.W / 2 + 1) / kTileBins;
-  int grid = num_sms() * 4;
-  if (grid > ntiles) grid = ntiles;
-  k_solve_f32<NMAX><<<grid, kTileBins * 32, smem, st>>>(p, certify ? 1 : 0);
+  k_solve_f32<NMAX><<<ntiles, kTileBins * 32, smem, st>>>(p, certify ? 1 : 0);
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_hp_t(const SolveParams& p, bool all_bins, cudaStream_t st) {
+cudaError_t launch_hp_t(const SolveParams& p, bool all_bins, int list, cudaStream_t st) {
   const size_t per_warp = hp_warp_elems<T>(p.N, p.C) * sizeof(cx<T>);
   int warps = (int)(96 * 1024 / per_warp);
   if (warps > 4) warps = 4;
@@ -338,8 +343,10 @@ cudaError_t launch_hp_t(const SolveParams& p, bool all_bins, cudaStream_t st) {
   const size_t smem = per_warp * warps;
   cudaError_t e = set_smem((const void*)k_solve_hp<T>, smem);
   if (e != cudaSuccess) return e;
-  const int grid = num_sms() * 8;
-  k_solve_hp<T><<<grid, warps * 32, smem, st>>>(p, all_bins ? 1 : 0, warps);
+  // one frequency per warp for the largest possible list (CTAs past the list length exit)
+  const int bins = p.H * (p.W / 2 + 1);
+  const int grid = (bins + warps - 1) / warps;
+  k_solve_hp<T><<<grid, warps * 32, smem, st>>>(p, all_bins ? 1 : 0, warps, list);
   return cudaGetLastError();
 }
 
@@ -351,8 +358,8 @@ cudaError_t launch_solve_f32(const SolveParams& p, bool certify, cudaStream_t st
   return launch_f32_n<32>(p, certify, st);
 }
 
-cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, cudaStream_t st) {
-  return f64 ? launch_hp_t<R64>(p, all_bins, st) : launch_hp_t<Rdf>(p, all_bins, st);
+cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, int list, cudaStream_t st) {
+  return f64 ? launch_hp_t<R64>(p, all_bins, list, st) : launch_hp_t<Rdf>(p, all_bins, list, st);
 }
 
 cudaError_t launch_exp_table(float4* table, cudaStream_t st) {

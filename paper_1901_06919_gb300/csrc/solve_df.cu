@@ -230,6 +230,14 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
       }
     }
 
+    // trace(G) >= largest eigenvalue, for the condition estimate
+    float tr = 0.f;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (SR(s) >= 0 && SR(s) == SL(s)) tr += G[s].re.hi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+
     // Cholesky on the slots
     bool ok = true;
     for (int k = 0; k < N; ++k) {
@@ -268,6 +276,77 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     for (int s = 0; s < S; ++s)
       if (SR(s) >= 0) Ls[lane + 32 * s] = pack(G[s]);
     __syncwarp();
+
+    // Condition estimate kappa ~ trace(G) |G^-1 v| after three steps of inverse iteration
+    // with the factor (FP32 is enough for an error estimate).
+    float kappa = 0.f;
+    if (p.err != nullptr) {
+      float2 v[R];
+#pragma unroll
+      for (int h = 0; h < R; ++h) {
+        const int r = lane + 32 * h;
+        v[h] = make_float2(0.f, 0.f);
+        if (r < N) {
+          float sn, cs;
+          sincospif(2.f * 0.6180339887f * (float)(r * r), &sn, &cs);
+          v[h] = make_float2(cs * rsqrtf((float)N), sn * rsqrtf((float)N));
+        }
+      }
+      float vnorm = 0.f;
+      for (int it = 0; it < 3; ++it) {
+        for (int k = 0; k < N; ++k) {
+          const float ikk = invd[k].x;
+          const int owner = k & 31, hk = k >> 5;
+          float2 mine = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < R; ++h)
+            if (h == hk) mine = v[h];
+          const float2 vk = make_float2(__shfl_sync(0xffffffffu, mine.x, owner) * ikk,
+                                        __shfl_sync(0xffffffffu, mine.y, owner) * ikk);
+#pragma unroll
+          for (int h = 0; h < R; ++h) {
+            const int r = lane + 32 * h;
+            if (r > k && r < N) {
+              const float4 l = Ls[col_start(k, N) + (r - k)];
+              cfms_c(v[h], make_float2(l.x, l.y), cconj(vk));
+            } else if (r == k) {
+              v[h] = vk;
+            }
+          }
+        }
+        for (int k = N - 1; k >= 0; --k) {
+          const float ikk = invd[k].x;
+          const int owner = k & 31, hk = k >> 5;
+          float2 mine = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < R; ++h)
+            if (h == hk) mine = v[h];
+          const float2 xk = make_float2(__shfl_sync(0xffffffffu, mine.x, owner) * ikk,
+                                        __shfl_sync(0xffffffffu, mine.y, owner) * ikk);
+#pragma unroll
+          for (int h = 0; h < R; ++h) {
+            const int r = lane + 32 * h;
+            if (r < k) {
+              const float4 l = Ls[col_start(r, N) + (k - r)];
+              cfms_c(v[h], make_float2(l.x, -l.y), cconj(xk));
+            } else if (r == k) {
+              v[h] = xk;
+            }
+          }
+        }
+        float n2 = 0.f;
+#pragma unroll
+        for (int h = 0; h < R; ++h)
+          if (lane + 32 * h < N) n2 += v[h].x * v[h].x + v[h].y * v[h].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        vnorm = sqrtf(n2);
+        const float inv = vnorm > 0.f ? 1.f / vnorm : 0.f;
+#pragma unroll
+        for (int h = 0; h < R; ++h) v[h] = cscale(v[h], inv);
+      }
+      kappa = tr * vnorm;
+    }
 
     // forward substitution L z = y, row r in lane r % 32
     for (int k = 0; k < N; ++k) {
@@ -316,15 +395,27 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     }
     const long long plane = (long long)p.H * (M + 1);
     const long long off = (long long)ky * (M + 1) + kx;
+    float n2 = 0.f;
 #pragma unroll
     for (int h = 0; h < R; ++h) {
       const int r = lane + 32 * h;
       if (r < N) {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (c < C)
-            p.x[((long long)r * C + c) * plane + off] =
+          if (c < C) {
+            const float2 xv =
                 ok ? make_float2(y[h][c].re.hi + y[h][c].re.lo, y[h][c].im.hi + y[h][c].im.lo) : make_float2(0.f, 0.f);
+            p.x[((long long)r * C + c) * plane + off] = xv;
+            n2 += xv.x * xv.x + xv.y * xv.y;
+          }
+      }
+    }
+    if (p.err != nullptr) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      if (lane == 0) {
+        p.err[q] = ok ? kappa * sqrtf(n2) : INFINITY;
+        p.xn2[q] = n2;
       }
     }
     if (lane == 0) {
@@ -347,10 +438,10 @@ cudaError_t launch_df_n(const SolveParams& p, bool all_bins, cudaStream_t st) {
   const size_t smem = per_warp * kDfWarps;
   cudaError_t e = set_smem((const void*)k_solve_df<NMAX, S>, smem);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_solve_df<NMAX, S><<<sms * 8, kDfWarps * 32, smem, st>>>(p, all_bins ? 1 : 0);
+  // one frequency per warp for the largest possible list: short CTAs let
+  // higher-priority streams interleave (CTAs past the list length exit at once)
+  const int bins = p.H * (p.W / 2 + 1);
+  k_solve_df<NMAX, S><<<(bins + kDfWarps - 1) / kDfWarps, kDfWarps * 32, smem, st>>>(p, all_bins ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -125,7 +125,9 @@ class _Batch:
 
     def __init__(self, H, W, C, cap, Nmax, device):
         self.H, self.W, self.C, self.cap, self.Nmax = H, W, C, cap, Nmax
-        self.stream = torch.cuda.Stream(device=device)
+        # the highest stream priority: admission fits run on default-priority streams, and
+        # their short CTAs let batches of requests be scheduled in between
+        self.stream = torch.cuda.Stream(device=device, priority=torch.cuda.Stream.priority_range()[1])
         self.host_desc = torch.zeros(cap * ct.sizeof(L.Request), dtype=torch.uint8).pin_memory()
         self.host_count = torch.zeros(1, dtype=torch.int32).pin_memory()
         self.dev_desc = torch.zeros(cap * ct.sizeof(L.Request), dtype=torch.uint8, device=device)
@@ -187,6 +189,7 @@ class Server:
                 b.capture()
         self.queue: dict[tuple, collections.deque] = {k: collections.deque() for k in self.classes}
         self.completed: list[Request] = []
+        self._fresh: list[Request] = []
         self.pts = {}
 
     def submit(self, r: Request):
@@ -209,6 +212,7 @@ class Server:
                         r.t_done = now
                         self.store.entries[r.fid].refs -= 1
                         self.completed.append(r)
+                        self._fresh.append(r)
                     b.requests = []
                     b.busy = False
 
@@ -255,9 +259,9 @@ class Server:
                 i += 1
             self.tick()
             if not keep_outputs:
-                for r in self.completed:
-                    if r.out is not None:
-                        self.release(r)
+                for r in self._fresh:
+                    self.release(r)
+            self._fresh.clear()
             if now - t0 > timeout_s:
                 raise TimeoutError("trace did not complete within the deadline")
         lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in trace])

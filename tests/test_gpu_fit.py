@@ -46,10 +46,12 @@ def test_small_scene_all_precisions(fdl, small_model_scene, precision):
     err = rel_l2(got, ref)
     assert err < TOL, err
     nb = 64 * 33
-    assert counts["fp32"] + counts["high_precision"] == nb
+    assert counts["fp32"] + counts["df"] + counts["fp64"] == nb
     assert counts["breakdown"] == 0 and counts["nonfinite"] == 0
-    if precision != "mixed":
-        assert counts["high_precision"] == nb
+    if precision == "df":
+        assert counts["df"] == nb
+    if precision == "f64":
+        assert counts["fp64"] == nb
 
 
 @pytest.mark.parametrize("reg", ["layer2", "l2"])
@@ -156,7 +158,7 @@ def test_full_size_dense_grid_sampled_bins(fdl):
     g = got[:, :, ky, kx]
     err = rel_l2(g, ref)
     assert err < TOL, err
-    assert counts["fp32"] + counts["high_precision"] == 512 * 257
+    assert counts["fp32"] + counts["df"] + counts["fp64"] == 512 * 257
     assert counts["breakdown"] == 0
 
 

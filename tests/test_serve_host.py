@@ -72,6 +72,7 @@ def test_drain_times_out_on_a_batch_that_never_completes():
     srv.classes = {(16, 16, 1): [_StuckBatch()]}
     srv.queue = {(16, 16, 1): collections.deque()}
     srv.completed = []
+    srv._fresh = []
     srv.store = FdlStore(1 << 20, "cpu")
     with pytest.raises(TimeoutError):
         srv.drain(timeout_s=0.05)

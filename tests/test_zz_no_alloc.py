@@ -37,7 +37,7 @@ def test_noalloc_fit_matches_workspace_fit_twice(fdl):
         D = torch.from_numpy(d.astype(np.float32)).cuda()
         S = fdl.rfft2(V)
         K, N = u.shape[0], d.size
-        opts = L.FitOpts(1e-2, 1e-4, L.REG["view2"], L.PREC["mixed"], 0.0)
+        opts = L.FitOpts(1e-2, 1e-4, L.REG["view2"], L.PREC["mixed"], 0.0, 0.0)
         ref, _ = fdl.fit_spectra(S, U, D, 1e-2, 1e-4)
         out = torch.full_like(ref, float("nan"))
         st = lib.fdl_fit_spectra_noalloc(_ptr(S), K, C, size, size, _ptr(U), _ptr(D), N, ct.byref(opts), _ptr(out),
@@ -53,6 +53,6 @@ def test_noalloc_rejects_frequencies_beyond_its_scratch(fdl):
 
     lib = L.load()
     p = ct.c_void_p(0x1000)  # never used: the size check fails first
-    opts = L.FitOpts(1e-2, 1e-4, 0, 0, 0.0)
+    opts = L.FitOpts(1e-2, 1e-4, 0, 0, 0.0, 0.0)
     st = lib.fdl_fit_spectra_noalloc(p, 9, 1, 2048, 1024, p, p, 8, ct.byref(opts), p, None)
     assert st == L.FDL_ENOMEM
