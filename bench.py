@@ -599,6 +599,23 @@ def cpu_baseline(views, u, d, s_list):
 
 
 # ------------------------------------------------------------------ main
+def max_over_ranks(value: float, device=None) -> float:
+    """The slowest rank's time: every rank contributes its own, all receive the maximum."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units processed by all ranks per second, in millions, over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3) / 1e6
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -675,12 +692,9 @@ def main():
     clocks.start()
     total_ms, stages = time_device_steps(path, args.steps, 0)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, device)
     ms = total_ms / args.steps
-    value = world * q_half() / (ms / 1e3) / 1e6
+    value = whole_job_rate(q_half(), world, ms)
 
     views_host = torch.from_numpy(views).pin_memory()
     e2e_ms, h2d, d2h = time_e2e(path, views_host, max(2, args.steps // 2), 1)
