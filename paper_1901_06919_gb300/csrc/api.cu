@@ -303,7 +303,7 @@ FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H,
   float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
   float2* nyq = cv.take<float2>((size_t)B * C * H);
   cudaError_t e = launch_pinhole_requests(req, layers, d, N, u0, B, out, (long long)C * H * W, st);
-  if (e == cudaSuccess) e = launch_render_spectra(req, B, nullptr, C, H, W, spec_split(main, nyq, H, W), st);
+  if (e == cudaSuccess) e = launch_render_spectra(req, B, nullptr, C, H, W, N, spec_split(main, nyq, H, W), st);
   if (e == cudaSuccess) e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, nullptr, C, st);
   if (e == cudaSuccess)
     e = launch_irfft_rows(main, out, (long long)B * C * H, H, W, 1.f / ((float)H * (float)W), nullptr, nullptr, C, st);
@@ -324,7 +324,7 @@ FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, 
   Carver cv(workspace);
   float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
   float2* nyq = cv.take<float2>((size_t)B * C * H);
-  cudaError_t e = launch_render_spectra(req, B, count, C, H, W, spec_split(main, nyq, H, W), st);
+  cudaError_t e = launch_render_spectra(req, B, count, C, H, W, Nmax, spec_split(main, nyq, H, W), st);
   if (e == cudaSuccess) e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, count, C, st);
   if (e == cudaSuccess)
     e = launch_irfft_rows(main, nullptr, (long long)B * C * H, H, W, 1.f / ((float)H * (float)W), req, count, C, st);

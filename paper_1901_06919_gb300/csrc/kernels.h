@@ -79,7 +79,9 @@ cudaError_t launch_select_fp64(const float* err, const float* xn2, int n, double
                                int* list, int* count, cudaStream_t st);
 
 // ---- render (render.cu) -----------------------------------------------------
-cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W,
+// Nmax: largest N of any request; sizes the shared layer tile used when all
+// requests read one FDL.
+cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
                                   SpecView out, cudaStream_t st);
 cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N,
                                     const float* u0, int B, float* out, long long img_elems, cudaStream_t st);

@@ -41,11 +41,27 @@ __device__ __forceinline__ float2 aperture_hat(int kind, float radius, const flo
   return make_float2(fx * fy, 0.f);
 }
 
-// CTA: 32 consecutive stored bins (lane = bin) x 8 warps; warp w renders
-// requests w, w + 8 gridDim.y, ...
-__global__ void __launch_bounds__(256) k_render(const fdl_request* __restrict__ req, int B,
-                                                const int* __restrict__ count, int C, int H, int W,
-                                                SpecView out) {
+// Phase of exp(+2 pi i d (u0 . w)) in cycles, reduced to [-1/2, 1/2], from
+// theta = u0 . w kept as a double-float (computed once per request and bin).
+__device__ __forceinline__ float phase_from_theta(df theta, float d) {
+  const df t = df_mul_f(theta, d);
+  const float n = rintf(t.hi);
+  return __fadd_rn(__fsub_rn(t.hi, n), t.lo);
+}
+
+constexpr int kRenderWarps = 8;
+constexpr int kTileMaxLC = 256;  // N * C of an FDL staged in shared memory
+
+// CTA: 32 consecutive stored bins (lane = bin) x 8 warps; warp w renders requests
+// w, w + 8, ...  When every request reads the same FDL (and N*C <= tile_lc) the
+// CTA stages that FDL's layer values for its 32 bins in shared memory once and all
+// requests read them there; otherwise each request reads its own layers from global.
+__global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request* __restrict__ req, int B,
+                                                              const int* __restrict__ count, int C, int H, int W,
+                                                              int tile_lc, SpecView out) {
+  extern __shared__ float2 tile[];  // [tile_lc][32]
+  __shared__ float dsh[64];
+  __shared__ int uniform;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = W >> 1;
   const int Qs = H * (M + 1);
@@ -55,26 +71,60 @@ __global__ void __launch_bounds__(256) k_render(const fdl_request* __restrict__ 
   bin_coords(valid ? q : 0, H, M, ky, kx);
   const float wy = freq_y(ky, H);
   const float wx = (float)kx / (float)W;
+  const float wabs = sqrtf(wx * wx + wy * wy);
   const long long plane = (long long)H * (M + 1);
   const long long off = (long long)ky * (M + 1) + kx;
   const int Bact = count ? min(*count, B) : B;
-  for (int b = blockIdx.y * 8 + warp; b < Bact; b += gridDim.y * 8) {
+  if (Bact <= 0) return;
+  if (threadIdx.x == 0) uniform = 1;
+  __syncthreads();
+  const float* L0 = req[0].layers;
+  const int N0 = req[0].N;
+  for (int b = threadIdx.x; b < Bact; b += blockDim.x)
+    if (req[b].layers != L0 || req[b].d != req[0].d) uniform = 0;
+  __syncthreads();
+  const bool shared = uniform && N0 * C <= tile_lc && N0 <= 64;
+  if (shared) {
+    const float2* x0 = reinterpret_cast<const float2*>(L0);
+    for (int e = threadIdx.x; e < N0 * C * 32; e += blockDim.x) {
+      const int lc = e >> 5, l2 = e & 31;
+      const int qq = blockIdx.x * 32 + l2;
+      float2 v = make_float2(0.f, 0.f);
+      if (qq < Qs) {
+        int yy, xx;
+        bin_coords(qq, H, M, yy, xx);
+        v = __ldg(x0 + (long long)lc * plane + (long long)yy * (M + 1) + xx);
+      }
+      tile[e] = v;
+    }
+    for (int k = threadIdx.x; k < N0; k += blockDim.x) dsh[k] = __ldg(req[0].d + k);
+    __syncthreads();
+  }
+  for (int b = warp; b < Bact; b += kRenderWarps) {
     const fdl_request r = req[b];
     const float2* x = reinterpret_cast<const float2*>(r.layers);
+    const df theta = df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy));
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+    const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
     for (int k = 0; k < r.N; ++k) {
-      const float dk = __ldg(r.d + k);
-      const float f = phase_cycles(r.u0x, r.u0y, wx, wy, dk);
+      const float dk = shared ? dsh[k] : __ldg(r.d + k);
       float2 sh;
-      sincospif(2.f * f, &sh.y, &sh.x);
+      sincospif(2.f * phase_from_theta(theta, dk), &sh.y, &sh.x);
       const float sd = r.s - dk;
-      const float2 coef = cmul(sh, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
+      float2 coef = sh;
+      if (r.aperture == FDL_AP_DISC && r.radius != 0.f) {
+        const float z = zscale * fabsf(sd);
+        coef = cscale(sh, z < 1e-3f ? 1.f - 0.125f * z * z : 2.f * j1f(z) / z);
+      } else if (r.aperture != FDL_AP_PINHOLE && r.aperture != FDL_AP_DISC) {
+        coef = cmul(sh, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
+      }
       if (valid) {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (c < C) cfma(acc[c], coef, __ldg(x + ((long long)k * C + c) * plane + off));
+          if (c < C)
+            cfma(acc[c], coef, shared ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off));
       }
     }
     if (valid) {
@@ -107,12 +157,14 @@ __global__ void k_pinhole_requests(fdl_request* req, const float* layers, const 
 
 }  // namespace
 
-cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W,
+cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
                                   SpecView out, cudaStream_t st) {
   const int Qs = H * (W / 2 + 1);
-  dim3 grid((Qs + 31) / 32, (B + 7) / 8);
-  if (grid.y > 65535) grid.y = 65535;
-  k_render<<<grid, 256, 0, st>>>(req, B, count, C, H, W, out);
+  const int tile_lc = min(Nmax * C, kTileMaxLC);
+  const size_t smem = (size_t)tile_lc * 32 * sizeof(float2);
+  cudaError_t e = set_smem((const void*)k_render, (size_t)kTileMaxLC * 32 * sizeof(float2));
+  if (e != cudaSuccess) return e;
+  k_render<<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, out);
   return cudaGetLastError();
 }
 

@@ -8,7 +8,7 @@
 // the smallest set of largest e_q whose removal brings the estimate of the
 // rest under budget * |X|:
 //   k_err_hist     histogram of log2 e_q: count and sum of e_q^2 per bucket;
-//   k_err_thresh   one thread scans the buckets from the top down;
+//   k_err_thresh   a prefix sum over the buckets gives the cut;
 //   k_err_compact  appends every frequency at or above the threshold.
 #include "kernels.h"
 
@@ -63,20 +63,53 @@ __global__ void __launch_bounds__(512) k_err_hist(const float* __restrict__ err,
 }
 
 // threshold: smallest e such that frequencies with e_q >= threshold go to FP64 and
-// u^2 * sum_{e_q < threshold} e_q^2 <= (budget^2) * sum |x|^2
-__global__ void k_err_thresh(const double* __restrict__ hist_sq, const unsigned int* __restrict__ hist_n,
-                             const double* __restrict__ xnorm2, double u, double budget, float* __restrict__ thresh) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double below = 0.0;
-  for (int b = 0; b < kBuckets - 1; ++b) below += hist_sq[b];
-  const double allow = budget * budget * xnorm2[0] / (u * u);
-  int cut = kBuckets - 1;  // bucket index from which everything goes to FP64 (+inf always)
-  while (cut > 0 && below > allow) {
-    --cut;
-    below -= hist_sq[cut];
+// u^2 * sum_{e_q < threshold} e_q^2 <= (budget^2) * sum |x|^2.
+// With P(c) = sum_{b < c} hist_sq[b] (nondecreasing in c), the cut bucket is the
+// largest c <= kBuckets - 1 with P(c) <= allowed; the last bucket (+inf, the
+// breakdowns) always goes to FP64.  One CTA of kThreshThreads threads scans the
+// buckets, kBuckets / kThreshThreads consecutive buckets per thread.
+constexpr int kThreshThreads = 512;
+constexpr int kPerThread = kBuckets / kThreshThreads;
+
+__global__ void __launch_bounds__(kThreshThreads) k_err_thresh(const double* __restrict__ hist_sq,
+                                                               const double* __restrict__ xnorm2, double u,
+                                                               double budget, float* __restrict__ thresh) {
+  __shared__ double warp_sum[kThreshThreads / 32];
+  __shared__ int cut;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double v[kPerThread];
+  double own = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    v[i] = hist_sq[t * kPerThread + i];
+    own += v[i];
   }
-  thresh[0] = exp2f((float)(cut - kBuckets / 2) / kPerOctave);
-  if (cut == kBuckets - 1) thresh[0] = INFINITY;  // only breakdowns
+  // inclusive scan of the per-thread sums: within the warp, then across warps
+  double inc = own;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_sum[warp] = inc;
+  if (t == 0) cut = 0;
+  __syncthreads();
+  double before = 0.0;
+  for (int w = 0; w < warp; ++w) before += warp_sum[w];
+  double p = before + inc - own;  // P(t * kPerThread)
+  const double allow = budget * budget * xnorm2[0] / (u * u);
+  int best = -1;
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const int c = t * kPerThread + i;
+    if (c <= kBuckets - 1 && p <= allow) best = c;
+    p += v[i];
+  }
+  if (best >= 0) atomicMax(&cut, best);
+  __syncthreads();
+  if (t == 0) {
+    const int c = cut;
+    thresh[0] = c == kBuckets - 1 ? INFINITY : exp2f((float)(c - kBuckets / 2) / kPerOctave);
+  }
 }
 
 __global__ void k_err_compact(const float* __restrict__ err, int n, const float* __restrict__ thresh,
@@ -106,7 +139,7 @@ cudaError_t launch_select_fp64(const float* err, const float* xn2, int n, double
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = sms * 2;
   k_err_hist<<<grid, 512, 0, st>>>(err, xn2, n, hist_sq, hist_n, xnorm2);
-  k_err_thresh<<<1, 32, 0, st>>>(hist_sq, hist_n, xnorm2, u, budget, thresh);
+  k_err_thresh<<<1, kThreshThreads, 0, st>>>(hist_sq, xnorm2, u, budget, thresh);
   k_err_compact<<<grid, 512, 0, st>>>(err, n, thresh, list, count);
   return cudaGetLastError();
 }
