@@ -65,11 +65,10 @@ extern "C" {
 #define FDL_REG_L2 2     /* Gamma = I (Sec. V-C)                                     */
 
 /* ---- arithmetic of the per-frequency solve ----------------------------- */
-#define FDL_PREC_MIXED 0 /* FP32 where the estimated condition number of
-                            A*A + lambda Gamma*Gamma is below kappa_max;
-                            double-float (FP32 pairs, ~2^-48) elsewhere,
-                            except the frequencies that native FP64 must
-                            take to meet df_error_budget                      */
+#define FDL_PREC_MIXED 0 /* FP32 everywhere the estimated FP32 error fits in
+                            f32_error_budget; double-float (FP32 pairs,
+                            ~2^-48) elsewhere, except the frequencies that
+                            native FP64 must take to meet df_error_budget     */
 #define FDL_PREC_DF 1    /* double-float at every frequency                   */
 #define FDL_PREC_F64 2   /* native FP64 at every frequency                    */
 #define FDL_PREC_F32 3   /* FP32 at every frequency, no certification         */
@@ -86,8 +85,10 @@ typedef struct fdl_fit_opts {
                        the diagonal is lambda (|w|^4 d^4 + eps)); unused otherwise */
   int reg;          /* FDL_REG_*                                                   */
   int precision;    /* FDL_PREC_*                                                  */
-  double kappa_max; /* FDL_PREC_MIXED: largest estimated condition number kept in
-                       FP32 (<= 0 selects the default, 100)                        */
+  double kappa_max; /* FDL_PREC_MIXED: largest estimated condition number of
+                       A*A + lambda Gamma*Gamma whose FP32 solution may be kept at
+                       all; above it the estimate itself is not trusted
+                       (<= 0 selects the default, 1e6)                             */
   double df_error_budget; /* FDL_PREC_MIXED: estimated relative L2 error that the
                              double-float frequencies may leave in the layers; the
                              frequencies with the largest estimated errors (condition
@@ -95,6 +96,12 @@ typedef struct fdl_fit_opts {
                              factorisation breaks down, are re-solved in native FP64
                              until the estimate of the rest is within it
                              (<= 0 selects the default, 4e-6; N <= 48 only)        */
+  double f32_error_budget; /* FDL_PREC_MIXED, N <= 32: the same for the FP32 pass:
+                              the frequencies with the largest estimated FP32
+                              errors (and those above kappa_max, with a
+                              factorisation that broke down or non-finite input)
+                              are re-solved in double-float until the estimate of
+                              the rest is within it (<= 0 selects the default, 2e-6) */
 } fdl_fit_opts;
 
 /* One image to render (Eq. BsFourier): the FDL it reads, the viewpoint u0,

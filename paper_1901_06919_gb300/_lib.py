@@ -19,7 +19,8 @@ APERTURE = {"pinhole": 0, "disc": 1, "square": 2, "points": 3}
 
 class FitOpts(ct.Structure):
     _fields_ = [("lam", ct.c_double), ("eps", ct.c_double), ("reg", ct.c_int), ("precision", ct.c_int),
-                ("kappa_max", ct.c_double), ("df_error_budget", ct.c_double)]
+                ("kappa_max", ct.c_double), ("df_error_budget", ct.c_double),
+                ("f32_error_budget", ct.c_double)]
 
 
 class Request(ct.Structure):

@@ -12,10 +12,18 @@ using namespace fdl;
 namespace {
 
 constexpr size_t kAlign = 256;
-// Error of the double-float solve per unit of (condition estimate x solution norm).
-// Measured: the bound kappa |x| 2^-47 overstates the error of the 7x7-view, 40-layer
-// solve about tenfold, so the estimate uses a tenth of 2^-47.
-constexpr double kDfUnit = 7.1e-16;
+// Error of the double-float solve per unit of (condition estimate x solution norm),
+// per square root of the number of views.  The Gram matrix and the right-hand side
+// are sums over the K views whose terms are nearly equal at the low, worst-conditioned
+// frequencies, so the rounding of the running sum grows like sqrt(K) in relative
+// terms.  Measured against extended-precision solutions at the frequencies with the
+// largest errors (kappa ~ 1e10): error / (kappa |x|) ~ 1.9e-15 at K = 49, 2.5e-15 at
+// K = 81 and 8e-15 at K = 361; 1.0e-16 sqrt(K) keeps the estimate at or above the
+// error of the layers over 49 to 361 views.
+constexpr double kDfUnitPerSqrtView = 1.0e-16;
+// Error of the FP32 solve per unit of (condition estimate x solution norm), about
+// 4 times the FP32 unit roundoff: the high quantiles of measured error / (kappa |x|).
+constexpr double kF32Unit = 4.5e-7;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -81,7 +89,8 @@ int check_fit_args(int K, int C, int H, int W, int N, const fdl_fit_opts* o) {
   if (o->reg < FDL_REG_VIEW2 || o->reg > FDL_REG_L2) return FDL_EINVAL;
   if (o->precision < FDL_PREC_MIXED || o->precision > FDL_PREC_F32) return FDL_EINVAL;
   if (o->precision == FDL_PREC_F32 && N > 32) return FDL_ENOTSUP;
-  if (std::isnan(o->kappa_max) || std::isnan(o->df_error_budget)) return FDL_EINVAL;
+  if (std::isnan(o->kappa_max) || std::isnan(o->df_error_budget) || std::isnan(o->f32_error_budget))
+    return FDL_EINVAL;
   return FDL_OK;
 }
 
@@ -102,22 +111,24 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
   p.lam_eps = (float)(o->lambda * (o->reg == FDL_REG_VIEW2 ? o->eps : 0.0));
   p.lam_d = o->lambda;
   p.lam_eps_d = o->lambda * (o->reg == FDL_REG_VIEW2 ? o->eps : 0.0);
-  p.kappa_max = (float)(o->kappa_max > 0.0 ? o->kappa_max : 100.0);
+  p.kappa_max = (float)(o->kappa_max > 0.0 ? o->kappa_max : 1e6);
   p.flagged = f.flagged;
   p.flagged64 = f.flagged64;
   p.err = nullptr;
   p.xn2 = nullptr;
   const double budget = o->df_error_budget > 0.0 ? o->df_error_budget : 4e-6;
+  const double budget32 = o->f32_error_budget > 0.0 ? o->f32_error_budget : 2e-6;
   p.counters = f.counters;
   p.exp_table = f.exp_table;
   cudaError_t e = cudaMemsetAsync(f.counters, 0, 16 * sizeof(int), st);
   if (e != cudaSuccess) return FDL_ECUDA;
   e = launch_exp_table(f.exp_table, st);
   if (e != cudaSuccess) return FDL_ECUDA;
-  // double-float: registers for N <= 48, shared memory beyond.  With the FP64 tier the
-  // double-float pass records an error scale per frequency; those with the largest
-  // estimated errors are then re-solved in native FP64 until the estimated error of the
-  // rest is within `budget` (relative L2 of the layers).
+  // Each tier records an error scale per frequency (condition estimate x solution
+  // norm); the frequencies with the largest estimated errors are re-solved in the next
+  // tier until the estimated error of the rest is within that tier's budget (relative
+  // L2 of the layers): FP32 -> double-float (registers for N <= 48, shared memory
+  // beyond) -> native FP64.
   const int Qs = H * (W / 2 + 1);
   auto solve_df = [&](bool all_bins, bool fp64_tier) {
     if (!solve_df_supported(N)) return launch_solve_hp(p, all_bins, false, 0, st);
@@ -126,11 +137,14 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
       p.err = f.err;
       p.xn2 = f.xn2;
       r = cudaMemsetAsync(f.err, 0, (size_t)Qs * sizeof(float), st);
-      if (r == cudaSuccess) r = cudaMemsetAsync(f.xn2, 0, (size_t)Qs * sizeof(float), st);
+      // after the FP32 pass xn2 already holds |x|^2 of every frequency (the
+      // double-float pass overwrites its own), so the budget is relative to all of X
+      if (r == cudaSuccess && all_bins) r = cudaMemsetAsync(f.xn2, 0, (size_t)Qs * sizeof(float), st);
     }
     if (r == cudaSuccess) r = launch_solve_df(p, all_bins, st);
     if (r == cudaSuccess && fp64_tier)
-      r = launch_select_fp64(f.err, f.xn2, Qs, kDfUnit, budget, f.select, f.flagged64, f.counters + 5, st);
+      r = launch_select_budget(f.err, f.xn2, Qs, kDfUnitPerSqrtView * std::sqrt((double)K), budget, f.select,
+                               f.flagged64, f.counters + 5, st);
     if (r == cudaSuccess && fp64_tier) r = launch_solve_hp(p, false, true, 1, st);
     return r;
   };
@@ -148,7 +162,11 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
       if (N > 32) {
         e = solve_df(true, true);
       } else {
+        p.err = f.err;
+        p.xn2 = f.xn2;
         e = launch_solve_f32(p, true, st);
+        if (e == cudaSuccess)
+          e = launch_select_budget(f.err, f.xn2, Qs, kF32Unit, budget32, f.select, f.flagged, f.counters + 4, st);
         if (e == cudaSuccess) e = solve_df(false, true);
       }
   }

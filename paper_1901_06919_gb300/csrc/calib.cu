@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(kCalibWarps * 32) k_calib(CalibParams cp) {
     }
     for (int j = 0; j < K; ++j) {
       const float2 uj = __ldg(reinterpret_cast<const float2*>(cp.u) + j);
-      const T th = theta_r(uj.x, uj.y, wx, wy, T{});
-      for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(mulf(th, __ldg(cp.d + r)), cp.exp_table);
+      const auto th = theta_r(uj.x, uj.y, wx, wy, T{});
+      for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(phase_r(th, __ldg(cp.d + r)), cp.exp_table);
       __syncwarp();
       if (lane < C) {
         const int c = lane;

@@ -28,12 +28,39 @@ __device__ __forceinline__ float layer2_gtg(int i, int l, int N) {
   return 0.f;
 }
 
-// theta = u . w in cycles per unit of disparity
+// theta = u . w in cycles per unit of disparity, and the phase d theta of
+// A_jk = exp(2 pi i d_k theta_j) (Eq. AMatGeneral).
+//
+// FP64: theta and d theta rounded once each (absolute phase error about
+// 2^-53 |d theta|).  Double-float: theta is kept unevaluated as the exact sum
+// p1 + e1 + p2 + e2 of two TwoProducts, each piece is multiplied by d exactly
+// (TwoProduct again), the two large products are reduced mod 1 exactly
+// (x - rint(x) is exact in floating point) and only then is everything
+// summed.  The phase then carries an absolute error of about 2^-48 however
+// large |d theta| is; rounding theta and d theta as double-floats instead
+// would leave 2^-47 |d theta|, which at |d theta| ~ 20 cycles (views at
+// |u| ~ 9) dominated the error of ill-conditioned frequencies.
 __device__ __forceinline__ R64 theta_r(float ux, float uy, float wx, float wy, R64) {
   return {(double)ux * (double)wx + (double)uy * (double)wy};
 }
-__device__ __forceinline__ Rdf theta_r(float ux, float uy, float wx, float wy, Rdf) {
-  return {df_add(two_prod(ux, wx), two_prod(uy, wy))};
+__device__ __forceinline__ R64 phase_r(R64 th, float d) { return {th.v * (double)d}; }
+
+struct ThetaX {
+  float p1, e1, p2, e2;
+};
+__device__ __forceinline__ ThetaX theta_r(float ux, float uy, float wx, float wy, Rdf) {
+  const df a = two_prod(ux, wx), b = two_prod(uy, wy);
+  return {a.hi, a.lo, b.hi, b.lo};
+}
+__device__ __forceinline__ Rdf phase_r(const ThetaX& t, float d) {
+  const df a = two_prod(d, t.p1), b = two_prod(d, t.p2);  // exact
+  const df c = two_prod(d, t.e1), e = two_prod(d, t.e2);  // exact, |c|, |e| <= 2^-24 |a|, |b|
+  const df s = two_sum(__fsub_rn(a.hi, rintf(a.hi)), __fsub_rn(b.hi, rintf(b.hi)));  // exact, |s| <= 1
+  const df m1 = two_sum(a.lo, b.lo);
+  const df m2 = two_sum(c.hi, e.hi);
+  df m = two_sum(m1.hi, m2.hi);
+  m.lo = __fadd_rn(m.lo, __fadd_rn(__fadd_rn(m1.lo, m2.lo), __fadd_rn(c.lo, e.lo)));
+  return {df_add(s, m)};
 }
 
 // exp(2 pi i t), FP64: CUDA's sincospi after reduction to [-1/2, 1/2].
@@ -103,8 +130,8 @@ __device__ bool hp_solve_bin(const HpProblem& p, int ky, int kx, cx<T>* G, cx<T>
   __syncwarp();
   for (int j = 0; j < p.K; ++j) {
     const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
-    const T th = theta_r(uj.x, uj.y, wx, wy, T{});
-    for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(mulf(th, __ldg(p.d + r)), p.exp_table);
+    const auto th = theta_r(uj.x, uj.y, wx, wy, T{});
+    for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(phase_r(th, __ldg(p.d + r)), p.exp_table);
     __syncwarp();
     float2 bj[4];
 #pragma unroll

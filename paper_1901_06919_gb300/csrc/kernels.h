@@ -52,15 +52,17 @@ struct SolveParams {
   float lam, lam_eps;  // lambda and lambda*eps
   double lam_d, lam_eps_d;
   float kappa_max;     // largest estimated condition number kept in FP32
-  int* flagged;        // bins for the double-float pass (written by the FP32 kernel)
+  int* flagged;        // bins for the double-float pass (chosen from the FP32 err / xn2)
   int* flagged64;      // bins for the native FP64 pass (chosen from err / xn2)
-  float* err;          // per bin: condition estimate x |x| of the double-float solve (nullable)
-  float* xn2;          // per bin: |x|^2 of the double-float solve
+  float* err;          // per bin: condition estimate x |x| of the last pass (nullable)
+  float* xn2;          // per bin: |x|^2 of the last pass that solved it
   int* counters;       // [0] FP32 bins, [1] double-float bins, [2] breakdowns, [3] non-finite,
                        // [4] double-float list length, [5] FP64 list length, [6] FP64 bins
   const float4* exp_table;  // df table of exp(2 pi i n / 1024), n in [0, 1024)
 };
-cudaError_t launch_solve_f32(const SolveParams& p, bool certify, cudaStream_t st);
+// FP32 solve of every stored bin; with estimate, also err / xn2 per bin (err = +inf
+// where the result is not trusted) and every bin counted in counters[0].
+cudaError_t launch_solve_f32(const SolveParams& p, bool estimate, cudaStream_t st);
 // Solves the bins of list `list` (0: p.flagged / counters[4], 1: p.flagged64 /
 // counters[5]) or, when all_bins, every stored bin; T = native FP64 when f64
 // else double-float (shared-memory matrix, any N <= 64).
@@ -71,12 +73,12 @@ cudaError_t launch_exp_table(float4* table, cudaStream_t st);
 bool solve_df_supported(int N);
 cudaError_t launch_solve_df(const SolveParams& p, bool all_bins, cudaStream_t st);
 
-// ---- FP64 selection (select.cu) ---------------------------------------------
+// ---- tier selection (select.cu) ---------------------------------------------
 // Appends to `list` the frequencies with the largest err so that the rest keep
 // u * sqrt(sum err^2) <= budget * sqrt(sum xn2); scratch of select_scratch_bytes().
 size_t select_scratch_bytes();
-cudaError_t launch_select_fp64(const float* err, const float* xn2, int n, double u, double budget, void* scratch,
-                               int* list, int* count, cudaStream_t st);
+cudaError_t launch_select_budget(const float* err, const float* xn2, int n, double u, double budget, void* scratch,
+                                 int* list, int* count, cudaStream_t st);
 
 // ---- render (render.cu) -----------------------------------------------------
 // Nmax: largest N of any request; sizes the shared layer tile used when all

@@ -1,12 +1,12 @@
-// Choice of the frequencies re-solved in native FP64.
+// Choice of the frequencies re-solved in the next precision tier
+// (FP32 -> double-float, double-float -> native FP64).
 //
-// The double-float solve records, per frequency q, an error scale
-// e_q = kappa_q |x_q| (condition estimate times solution norm; 0 for
-// frequencies solved elsewhere, +inf where its factorisation broke down) and
-// |x_q|^2.  With u the double-float unit of the solve, the
-// estimated error of the layers is sqrt(sum (u e_q)^2).  These kernels pick
-// the smallest set of largest e_q whose removal brings the estimate of the
-// rest under budget * |X|:
+// A solve pass records, per frequency q, an error scale e_q = kappa_q |x_q|
+// (condition estimate times solution norm; 0 for frequencies solved
+// elsewhere, +inf where its result is not trusted) and |x_q|^2.  With u the
+// error of that pass per unit of e_q, the estimated error of the layers is
+// sqrt(sum (u e_q)^2).  These kernels pick the smallest set of largest e_q
+// whose removal brings the estimate of the rest under budget * |X|:
 //   k_err_hist     histogram of log2 e_q: count and sum of e_q^2 per bucket;
 //   k_err_thresh   a prefix sum over the buckets gives the cut;
 //   k_err_compact  appends every frequency at or above the threshold.
@@ -126,8 +126,8 @@ __global__ void k_err_compact(const float* __restrict__ err, int n, const float*
 
 size_t select_scratch_bytes() { return kBuckets * (sizeof(double) + sizeof(unsigned int)) + 64; }
 
-cudaError_t launch_select_fp64(const float* err, const float* xn2, int n, double u, double budget, void* scratch,
-                               int* list, int* count, cudaStream_t st) {
+cudaError_t launch_select_budget(const float* err, const float* xn2, int n, double u, double budget, void* scratch,
+                                 int* list, int* count, cudaStream_t st) {
   double* hist_sq = static_cast<double*>(scratch);
   unsigned int* hist_n = reinterpret_cast<unsigned int*>(hist_sq + kBuckets);
   double* xnorm2 = reinterpret_cast<double*>(hist_n + kBuckets);

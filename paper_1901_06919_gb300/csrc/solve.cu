@@ -8,10 +8,12 @@
 //
 // Two kernels:
 //  * k_solve_f32: FP32, one warp per frequency, lane i owns row i of the
-//    Hermitian matrix in registers.  It estimates the condition number from
-//    the factor (Gershgorin bound on the largest eigenvalue, three steps of
-//    inverse iteration for the smallest) and keeps the FP32 result only when
-//    the estimate is below kappa_max; other frequencies go to a list.
+//    Hermitian matrix in registers.  With estimate set it also records, per
+//    frequency, an error scale kappa |x| (kappa from three steps of power
+//    iteration for the largest eigenvalue and three steps of inverse
+//    iteration with the factor for the smallest; +inf where the factorisation
+//    broke down, the input was not finite or kappa exceeds kappa_max) and |x|^2,
+//    from which the caller picks the frequencies to re-solve more precisely.
 //  * k_solve_hp<T>: the same solve in double-float (T = Rdf) or native FP64
 //    (T = R64) for the listed frequencies (or for all of them).
 #include "hp_solve.cuh"
@@ -25,7 +27,7 @@ constexpr int kViewChunk = 32;  // views staged per pass
 
 // ------------------------------------------------------------------ FP32
 template <int NMAX>
-__global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int certify) {
+__global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int estimate) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -37,8 +39,6 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
   float2* Ls = arow + kTileBins * NMAX;                                 // [kTileBins][NMAX][NMAX+1]
   float2* myA = arow + warp * NMAX;
   float2* myL = Ls + warp * NMAX * (NMAX + 1);
-  __shared__ int tile_flag[kTileBins];
-  __shared__ int tile_base;
   __shared__ int cnt_local[4];
   if (threadIdx.x < 4) cnt_local[threadIdx.x] = 0;
 
@@ -116,13 +116,35 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
         }
       }
     }
-    // Gershgorin bound of the largest eigenvalue
-    float rowsum = 0.f;
+    // largest eigenvalue: power iteration from a vector with a component along
+    // every eigenvector in practice (all-ones plus golden-angle phases)
+    float lmax = 0.f;
+    if (estimate) {
+      float2 v = make_float2(0.f, 0.f);
+      if (lane < N) {
+        float sn, cs;
+        sincospif(2.f * 0.6180339887f * (float)(lane * lane), &sn, &cs);
+        v = make_float2(1.f + cs, sn);
+      }
+      for (int it = 0; it < 3; ++it) {
+        float2 w = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int l = 0; l < NMAX; ++l) rowsum += fabsf(G[l].x) + fabsf(G[l].y);
-    if (lane >= N) rowsum = 0.f;
+        for (int l = 0; l < NMAX; ++l) {
+          const float2 vl = make_float2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
+          if (l < N) cfma(w, G[l], vl);
+        }
+        float n2 = lane < N ? w.x * w.x + w.y * w.y : 0.f;
+        float v2 = lane < N ? v.x * v.x + v.y * v.y : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rowsum = fmaxf(rowsum, __shfl_xor_sync(0xffffffffu, rowsum, o));
+        for (int o = 16; o > 0; o >>= 1) {
+          n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+          v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+        }
+        lmax = v2 > 0.f ? sqrtf(n2 / v2) : 0.f;  // |G v| / |v|
+        const float inv = n2 > 0.f ? rsqrtf(n2) : 0.f;
+        v = lane < N ? cscale(w, inv) : make_float2(0.f, 0.f);
+      }
+    }
 
     // Cholesky G = L L*, row i in lane i
     bool ok = true;
@@ -205,35 +227,35 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       const float inv = vnorm > 0.f ? 1.f / vnorm : 0.f;
       v = cscale(v, inv);
     }
-    const float kappa = rowsum * vnorm;
-    const bool keep = !certify || (ok && finite && kappa <= p.kappa_max && isfinite(kappa));
-    // without certification a factorisation that broke down leaves zeros
-    const bool broke = !certify && !ok;
-    if (keep && lane < N) {
-      const long long plane = (long long)p.H * (M + 1);
-      const long long off = (long long)ky * (M + 1) + kx;
+    const long long plane = (long long)p.H * (M + 1);
+    const long long off = (long long)ky * (M + 1) + kx;
+    // without the estimate a factorisation that broke down leaves zeros
+    const bool broke = !ok;
+    if (lane < N) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         if (c < C) p.x[((long long)lane * C + c) * plane + off] = broke ? make_float2(0.f, 0.f) : y[c];
     }
-    // tile bookkeeping: one atomic per tile for the list
+    if (estimate) {
+      float n2 = 0.f;
+      if (lane < N) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < C) n2 += y[c].x * y[c].x + y[c].y * y[c].y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      const float kappa = lmax * vnorm;
+      const bool trusted = ok && finite && isfinite(kappa) && kappa <= p.kappa_max && isfinite(n2);
+      if (lane == 0) {
+        p.err[q] = trusted ? kappa * sqrtf(n2) : INFINITY;
+        p.xn2[q] = isfinite(n2) ? n2 : 0.f;
+      }
+    }
     if (lane == 0) {
-      tile_flag[warp] = keep ? 0 : 1;
-      if (keep && !broke) atomicAdd(&cnt_local[0], 1);
-      if (broke) atomicAdd(&cnt_local[2], 1);
+      if (estimate || !broke) atomicAdd(&cnt_local[0], 1);
+      if (!estimate && broke) atomicAdd(&cnt_local[2], 1);
       if (!finite) atomicAdd(&cnt_local[3], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int nf = 0;
-      for (int w = 0; w < kTileBins; ++w) nf += tile_flag[w];
-      tile_base = nf ? atomicAdd(p.counters + 4, nf) : 0;
-    }
-    __syncthreads();
-    if (lane == 0 && tile_flag[warp]) {
-      int pos = tile_base;
-      for (int w = 0; w < warp; ++w) pos += tile_flag[w];
-      p.flagged[pos] = q;
     }
   }
   __syncthreads();
@@ -323,14 +345,14 @@ int num_sms() {
 }
 
 template <int NMAX>
-cudaError_t launch_f32_n(const SolveParams& p, bool certify, cudaStream_t st) {
+cudaError_t launch_f32_n(const SolveParams& p, bool estimate, cudaStream_t st) {
   const size_t smem = (size_t)(kViewChunk * 4 * kTileBins + kTileBins * NMAX +
                                kTileBins * NMAX * (NMAX + 1)) * sizeof(float2);
   cudaError_t e = set_smem((const void*)k_solve_f32<NMAX>, smem);
   if (e != cudaSuccess) return e;
   // one tile per CTA: short CTAs let higher-priority work interleave
   const int ntiles = p.H * (p.W / 2 + 1) / kTileBins;
-  k_solve_f32<NMAX><<<ntiles, kTileBins * 32, smem, st>>>(p, certify ? 1 : 0);
+  k_solve_f32<NMAX><<<ntiles, kTileBins * 32, smem, st>>>(p, estimate ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -352,10 +374,10 @@ cudaError_t launch_hp_t(const SolveParams& p, bool all_bins, int list, cudaStrea
 
 }  // namespace
 
-cudaError_t launch_solve_f32(const SolveParams& p, bool certify, cudaStream_t st) {
-  if (p.N <= 8) return launch_f32_n<8>(p, certify, st);
-  if (p.N <= 16) return launch_f32_n<16>(p, certify, st);
-  return launch_f32_n<32>(p, certify, st);
+cudaError_t launch_solve_f32(const SolveParams& p, bool estimate, cudaStream_t st) {
+  if (p.N <= 8) return launch_f32_n<8>(p, estimate, st);
+  if (p.N <= 16) return launch_f32_n<16>(p, estimate, st);
+  return launch_f32_n<32>(p, estimate, st);
 }
 
 cudaError_t launch_solve_hp(const SolveParams& p, bool all_bins, bool f64, int list, cudaStream_t st) {

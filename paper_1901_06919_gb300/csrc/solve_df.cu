@@ -133,12 +133,15 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
   float4* Ls = col + NMAX;                       // packed lower triangle, column-major
   float2* invd = reinterpret_cast<float2*>(Ls + NMAX * (NMAX + 1) / 2);  // 1 / L_kk as df
 
-  // coordinates (r, l) of this lane's slots, packed as r * 256 + l (-1: unused slot)
+  // coordinates (r, l) of this lane's slots, packed as r * 256 + l.  An unused slot
+  // (entry number >= E) gets (N, N): it reads Arow[N] / col[N], which lie inside this
+  // warp's shared region and are zeroed below, so the Gram loop needs no branch; it
+  // never matches a pivot column k < N and is never stored.
   int rl[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int e = lane + 32 * s;
-    rl[s] = -1;
+    rl[s] = (N << 8) | N;
     if (e < E) {
       int l = 0;
       while (col_start(l + 1, N) <= e) ++l;
@@ -146,7 +149,10 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     }
   }
 #define SR(s) (rl[s] >> 8)
-#define SL(s) (rl[s] < 0 ? -1 : (rl[s] & 255))
+#define SL(s) (rl[s] & 255)
+#define SLOT_USED(s) (lane + 32 * (s) < E)
+  for (int i = lane; i < 2 * NMAX + 1; i += 32) Arow[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncwarp();
   const float4* tab = p.exp_table;
   const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(p.counters + 4));
   int nhp = 0, nbad = 0;
@@ -169,10 +175,13 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     float dr[R];
 #pragma unroll
     for (int h = 0; h < R; ++h) dr[h] = (lane + 32 * h < N) ? __ldg(p.d + lane + 32 * h) : 0.f;
+    dfc Ssum[R];  // S_r = sum_j (A_jr - 1)
+#pragma unroll
+    for (int h = 0; h < R; ++h) Ssum[h] = {{0.f, 0.f}, {0.f, 0.f}};
 
     for (int j = 0; j < K; ++j) {
       const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
-      const Rdf th = theta_r(uj.x, uj.y, wx, wy, Rdf{});
+      const ThetaX th = theta_r(uj.x, uj.y, wx, wy, Rdf{});
       float2 bj[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) bj[c] = c < C ? *p.b.at((long long)j * C + c, ky, kx, M) : make_float2(0.f, 0.f);
@@ -180,30 +189,90 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
       for (int h = 0; h < R; ++h) {
         const int r = lane + 32 * h;
         if (r < N) {
-          const cx<Rdf> a = cexp2pi(mulf(th, dr[h]), tab);
-          const float4 av = make_float4(a.re.v.hi, a.im.v.hi, a.re.v.lo, a.im.v.lo);
+          const cx<Rdf> a = cexp2pi(phase_r(th, dr[h]), tab);
+          // A - 1: the subtraction of the high word is exact (TwoSum)
+          const df t = two_sum(a.re.v.hi, -1.f);
+          const df am = two_sum(t.hi, __fadd_rn(t.lo, a.re.v.lo));
+          const float4 av = make_float4(am.hi, a.im.v.hi, am.lo, a.im.v.lo);
           Arow[r] = av;
+          {
+            const df s1 = two_sum(Ssum[h].re.hi, am.hi);
+            Ssum[h].re = two_sum(s1.hi, __fadd_rn(__fadd_rn(Ssum[h].re.lo, s1.lo), am.lo));
+            const df s2 = two_sum(Ssum[h].im.hi, a.im.v.hi);
+            Ssum[h].im = two_sum(s2.hi, __fadd_rn(__fadd_rn(Ssum[h].im.lo, s2.lo), a.im.v.lo));
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c)
             if (c < C) rhs_acc(y[h][c], av, bj[c]);
         }
       }
       __syncwarp();
+      // every slot, without a branch, so that the independent slot updates interleave;
+      // diagonal slots are overwritten below (the sum of |A_jk|^2 is exactly K)
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        if (SR(s) > SL(s)) {  // off-diagonal: the diagonal sum of |A_jk|^2 is exactly K
-          gram_acc(G[s], Arow[SR(s)], Arow[SL(s)]);
-          // keep |lo| within an ulp of |hi| so that the low word's own rounding stays at 2^-48
-          G[s].re = fast_two_sum(G[s].re.hi, G[s].re.lo);
-          G[s].im = fast_two_sum(G[s].im.hi, G[s].im.lo);
-        }
+        gram_acc(G[s], Arow[SR(s)], Arow[SL(s)]);
+        // keep |lo| within an ulp of |hi| so that the low word's own rounding stays at 2^-48
+        G[s].re = fast_two_sum(G[s].re.hi, G[s].re.lo);
+        G[s].im = fast_two_sum(G[s].im.hi, G[s].im.lo);
       }
       __syncwarp();
     }
+    // Assemble A*A and A*b from the sums over (A - 1).  With a = 1 + a~,
+    //   conj(a_r) a_l = 1 + conj(a~_r) + a~_l + conj(a~_r) a~_l,
+    // so G_rl = K + conj(S_r) + S_l + sum_j conj(a~_jr) a~_jl and
+    // y_r = sum_j b_j + sum_j conj(a~_jr) b_j.  At the low, worst-conditioned
+    // frequencies every A_jk is close to 1 and the sums over a~ stay small, so
+    // their rounding does not grow with the number of views the way the
+    // running sums of nearly equal terms of A*A and A*b would.
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+      if (lane + 32 * h < N) col[lane + 32 * h] = pack(Ssum[h]);
+    __syncwarp();
+    const df Kdf = {(float)K, 0.f};
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       renorm(G[s]);
-      if (SR(s) >= 0 && SR(s) == SL(s)) G[s] = {{(float)K, 0.f}, {0.f, 0.f}};
+      if (SR(s) == SL(s)) {
+        G[s] = {Kdf, {0.f, 0.f}};  // sum_j |A_jk|^2 = K exactly
+      } else {
+        const dfc sr = unpack(col[SR(s)]), sl = unpack(col[SL(s)]);
+        G[s].re = df_add(G[s].re, df_add(Kdf, df_add(sr.re, sl.re)));
+        G[s].im = df_add(G[s].im, df_sub(sl.im, sr.im));
+      }
+    }
+    // sum_j b_j per channel: lanes over views, then a butterfly of double-float adds
+    {
+      dfc bs[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bs[c] = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int j = lane; j < K; j += 32) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c < C) {
+            const float2 bv = *p.b.at((long long)j * C + c, ky, kx, M);
+            bs[c].re = df_add_f(bs[c].re, bv.x);
+            bs[c].im = df_add_f(bs[c].im, bv.y);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < C) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float4 v = shfl4(pack(bs[c]), lane ^ o);
+            const dfc w = unpack(v);
+            bs[c].re = df_add(bs[c].re, w.re);
+            bs[c].im = df_add(bs[c].im, w.im);
+          }
+#pragma unroll
+          for (int h = 0; h < R; ++h) {
+            y[h][c].re = df_add(y[h][c].re, bs[c].re);
+            y[h][c].im = df_add(y[h][c].im, bs[c].im);
+          }
+        }
+      }
     }
 
     // lambda Gamma*Gamma
@@ -215,7 +284,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const int r = SR(s), l = SL(s);
-        if (r < 0) continue;
+        if (r >= N) continue;
         if (p.reg == 0) {
           if (r == l) {
             const float dv = __ldg(p.d + r);
@@ -234,7 +303,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     float tr = 0.f;
 #pragma unroll
     for (int s = 0; s < S; ++s)
-      if (SR(s) >= 0 && SR(s) == SL(s)) tr += G[s].re.hi;
+      if (SR(s) < N && SR(s) == SL(s)) tr += G[s].re.hi;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
 
@@ -274,7 +343,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
-      if (SR(s) >= 0) Ls[lane + 32 * s] = pack(G[s]);
+      if (SLOT_USED(s)) Ls[lane + 32 * s] = pack(G[s]);
     __syncwarp();
 
     // Condition estimate kappa ~ trace(G) |G^-1 v| after three steps of inverse iteration
@@ -426,8 +495,11 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
   }
 #undef SR
 #undef SL
+#undef SLOT_USED
   if (lane == 0) {
     if (nhp) atomicAdd(p.counters + 1, nhp);
+    // a listed frequency was first solved (and counted) by the FP32 pass
+    if (nhp && !all_bins) atomicSub(p.counters + 0, nhp);
     if (nbad) atomicAdd(p.counters + 2, nbad);
   }
 }

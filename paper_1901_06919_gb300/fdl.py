@@ -43,8 +43,9 @@ def workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
-def _opts(lam, eps, reg, precision, kappa_max, df_error_budget=0.0) -> L.FitOpts:
-    return L.FitOpts(float(lam), float(eps), L.REG[reg], L.PREC[precision], float(kappa_max), float(df_error_budget))
+def _opts(lam, eps, reg, precision, kappa_max, df_error_budget=0.0, f32_error_budget=0.0) -> L.FitOpts:
+    return L.FitOpts(float(lam), float(eps), L.REG[reg], L.PREC[precision], float(kappa_max), float(df_error_budget),
+                     float(f32_error_budget))
 
 
 # ---------------------------------------------------------------- DFTs
@@ -87,8 +88,9 @@ class FitWorkspace:
 
 
 def fit(views: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, eps: float = 1e-4,
-        reg: str = "view2", precision: str = "mixed", kappa_max: float = 100.0,
-        out: torch.Tensor | None = None, ws: FitWorkspace | None = None, stream=None, df_error_budget: float = 0.0):
+        reg: str = "view2", precision: str = "mixed", kappa_max: float = 0.0,
+        out: torch.Tensor | None = None, ws: FitWorkspace | None = None, stream=None, df_error_budget: float = 0.0,
+        f32_error_budget: float = 0.0):
     """Layer construction (Sec. V-A) of ``views [K][C][H][W]``; returns ``(layers, workspace)``."""
     _need(views, torch.float32, "views", 4)
     _need(u, torch.float32, "u", 2)
@@ -101,16 +103,16 @@ def fit(views: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, eps: 
     need = lib.fdl_fit_workspace_size(K, C, H, W, N)
     if ws is None or ws.buf.numel() < need:
         ws = FitWorkspace(workspace(need, views.device))
-    o = _opts(lam, eps, reg, precision, kappa_max, df_error_budget)
+    o = _opts(lam, eps, reg, precision, kappa_max, df_error_budget, f32_error_budget)
     L.check(lib.fdl_fit(_p(views), K, C, H, W, _p(u), _p(d), N, ct.byref(o), _p(out), _p(ws.buf),
                         ws.buf.numel(), _stream(stream)), "fdl_fit")
     return out, ws
 
 
 def fit_spectra(spectra: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, eps: float = 1e-4,
-                reg: str = "view2", precision: str = "mixed", kappa_max: float = 100.0,
+                reg: str = "view2", precision: str = "mixed", kappa_max: float = 0.0,
                 out: torch.Tensor | None = None, ws: FitWorkspace | None = None, stream=None,
-                df_error_budget: float = 0.0):
+                df_error_budget: float = 0.0, f32_error_budget: float = 0.0):
     """Per-frequency solve from half spectra ``[K][C][H][W//2+1]``; returns ``(layers, workspace)``."""
     _need(spectra, torch.complex64, "spectra", 4)
     _need(u, torch.float32, "u", 2)
@@ -124,7 +126,7 @@ def fit_spectra(spectra: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: fl
     need = lib.fdl_fit_spectra_workspace_size(K, C, H, W, N)
     if ws is None or ws.buf.numel() < need:
         ws = FitWorkspace(workspace(need, spectra.device))
-    o = _opts(lam, eps, reg, precision, kappa_max, df_error_budget)
+    o = _opts(lam, eps, reg, precision, kappa_max, df_error_budget, f32_error_budget)
     L.check(lib.fdl_fit_spectra(_p(spectra), K, C, H, W, _p(u), _p(d), N, ct.byref(o), _p(out), _p(ws.buf),
                                 ws.buf.numel(), _stream(stream)), "fdl_fit_spectra")
     return out, ws

@@ -58,9 +58,10 @@ def test_workspace_queries(lib):
 
 
 def _opts(**kw):
-    o = dict(lam=1e-2, eps=1e-4, reg=0, precision=0, kappa_max=0.0, df_error_budget=0.0)
+    o = dict(lam=1e-2, eps=1e-4, reg=0, precision=0, kappa_max=0.0, df_error_budget=0.0, f32_error_budget=0.0)
     o.update(kw)
-    return L.FitOpts(o["lam"], o["eps"], o["reg"], o["precision"], o["kappa_max"], o["df_error_budget"])
+    return L.FitOpts(o["lam"], o["eps"], o["reg"], o["precision"], o["kappa_max"], o["df_error_budget"],
+                     o["f32_error_budget"])
 
 
 def test_fit_rejects_bad_arguments_before_any_launch(lib):
@@ -80,6 +81,7 @@ def test_fit_rejects_bad_arguments_before_any_launch(lib):
     assert call(opts=_opts(precision=9)) == L.FDL_EINVAL
     assert call(opts=_opts(precision=3), N=40) == L.FDL_ENOTSUP
     assert call(opts=_opts(df_error_budget=float("nan"))) == L.FDL_EINVAL
+    assert call(opts=_opts(f32_error_budget=float("nan"))) == L.FDL_EINVAL
     assert call(views=ct.c_void_p(0)) == L.FDL_EINVAL
     assert call(ws=1024) == L.FDL_ENOMEM
 
@@ -104,4 +106,4 @@ def test_request_struct_layout_matches_header(lib):
     # fdl_request: 4 pointers, 3 ints, 4 floats, 1 int
     assert ct.sizeof(L.Request) == 64
     assert L.Request.u0x.offset == 44
-    assert ct.sizeof(L.FitOpts) == 40
+    assert ct.sizeof(L.FitOpts) == 48
