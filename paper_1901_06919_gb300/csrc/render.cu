@@ -52,15 +52,46 @@ __device__ __forceinline__ float phase_from_theta(df theta, float d) {
 constexpr int kRenderWarps = 8;
 constexpr int kTileMaxLC = 256;  // N * C of an FDL staged in shared memory
 
-// CTA: 32 consecutive stored bins (lane = bin) x 8 warps; warp w renders requests
-// w, w + 8, ...  When every request reads the same FDL (and N*C <= tile_lc) the
-// CTA stages that FDL's layer values for its 32 bins in shared memory once and all
-// requests read them there; otherwise each request reads its own layers from global.
+// sum over layers k = k0, k0 + kstep, ... < r.N of the Eq. BsFourier terms of request r at
+// this lane's frequency; layer values from the shared tile when given, else from global
+__device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
+                                             float wx, float wabs, long long plane, long long off, bool valid,
+                                             const float2* tile, const float* dsh, int lane, float2 acc[4]) {
+  const float2* x = reinterpret_cast<const float2*>(r.layers);
+  const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
+  for (int k = k0; k < r.N; k += kstep) {
+    const float dk = tile ? dsh[k] : __ldg(r.d + k);
+    float2 sh;
+    sincospif(2.f * phase_from_theta(theta, dk), &sh.y, &sh.x);
+    const float sd = r.s - dk;
+    float2 coef = sh;
+    if (r.aperture == FDL_AP_DISC && r.radius != 0.f) {
+      const float z = zscale * fabsf(sd);
+      coef = cscale(sh, z < 1e-3f ? 1.f - 0.125f * z * z : 2.f * j1f(z) / z);
+    } else if (r.aperture != FDL_AP_PINHOLE && r.aperture != FDL_AP_DISC) {
+      coef = cmul(sh, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
+    }
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < C) cfma(acc[c], coef, tile ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off));
+    }
+  }
+}
+
+// CTA: 32 consecutive stored bins (lane = bin) x 8 warps.
+//  * B >= 8 requests: warp w renders requests w, w + 8, ...; when every request reads
+//    the same FDL (and N*C <= tile_lc) the CTA first stages that FDL's layer values for
+//    its 32 bins in shared memory and all requests read them there.
+//  * B < 8 (single renders, small batches): the 8 / B warps given to a request split its
+//    layers and their partial sums are added through shared memory, so that one request
+//    still occupies the whole CTA.
 __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request* __restrict__ req, int B,
                                                               const int* __restrict__ count, int C, int H, int W,
                                                               int tile_lc, SpecView out) {
   extern __shared__ float2 tile[];  // [tile_lc][32]
   __shared__ float dsh[64];
+  __shared__ float2 part[kRenderWarps][4][32];
   __shared__ int uniform;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = W >> 1;
@@ -76,6 +107,33 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   const long long off = (long long)ky * (M + 1) + kx;
   const int Bact = count ? min(*count, B) : B;
   if (Bact <= 0) return;
+
+  if (Bact < kRenderWarps) {
+    const int G = kRenderWarps / Bact;  // warps per request
+    const int b = warp / G, sl = warp - b * G;
+    float2 acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+    if (b < Bact) {
+      const fdl_request r = req[b];
+      const df theta = df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy));
+      render_terms(r, sl, G, C, theta, wy, wx, wabs, plane, off, valid, nullptr, nullptr, lane, acc);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) part[warp][c][lane] = acc[c];
+    __syncthreads();
+    if (b < Bact && sl == 0 && valid) {
+      for (int w = 1; w < G; ++w) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = cadd(acc[c], part[warp + w][c][lane]);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < C) *out.at((long long)b * C + c, ky, kx, M) = acc[c];
+    }
+    return;
+  }
+
   if (threadIdx.x == 0) uniform = 1;
   __syncthreads();
   const float* L0 = req[0].layers;
@@ -102,31 +160,11 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   }
   for (int b = warp; b < Bact; b += kRenderWarps) {
     const fdl_request r = req[b];
-    const float2* x = reinterpret_cast<const float2*>(r.layers);
     const df theta = df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy));
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
-    const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
-    for (int k = 0; k < r.N; ++k) {
-      const float dk = shared ? dsh[k] : __ldg(r.d + k);
-      float2 sh;
-      sincospif(2.f * phase_from_theta(theta, dk), &sh.y, &sh.x);
-      const float sd = r.s - dk;
-      float2 coef = sh;
-      if (r.aperture == FDL_AP_DISC && r.radius != 0.f) {
-        const float z = zscale * fabsf(sd);
-        coef = cscale(sh, z < 1e-3f ? 1.f - 0.125f * z * z : 2.f * j1f(z) / z);
-      } else if (r.aperture != FDL_AP_PINHOLE && r.aperture != FDL_AP_DISC) {
-        coef = cmul(sh, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
-      }
-      if (valid) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c < C)
-            cfma(acc[c], coef, shared ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off));
-      }
-    }
+    render_terms(r, 0, 1, C, theta, wy, wx, wabs, plane, off, valid, shared ? tile : nullptr, dsh, lane, acc);
     if (valid) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
