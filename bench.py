@@ -700,15 +700,15 @@ def main():
     e2e_ms, h2d, d2h = time_e2e(path, views_host, max(2, args.steps // 2), 1)
     legs = time_kernel_legs(path)
     p50, p99 = time_latency(path)
-    launches = 0
-    # kernels per step: fit = rows + cols + exp table + solve f32 + solve hp (+1 memset);
+    # kernels per step: fit = 2 twiddle tables + rows + cols + exp table + FP32 solve + 3 selection
+    # + moment check + 2 double-float solves (one exits at once) + 3 selection + FP64 solve;
     # render = requests + render + cols + rows; refocus = render + cols + rows
-    launches = 5 + 4 + 3
+    launches = 16 + 4 + 3
 
     fit_ms = stages["fit_ms"]
     render_ms = stages["render81_ms"] + stages["refocus32_ms"]
     # roofline: the high-precision solve (dominant kernel), double-float work counted on the FP32 pipe
-    rl = roofline_entry(legs, clk)
+    rl = roofline_entry(legs, clk, moment_form_applies(u, d))
     line = {
         "metric": METRIC, "value": value, "unit": "Mfreq/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -751,31 +751,62 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def df_ops_per_frequency(K, N, C):
-    """FP32 operations of the double-float solve at one frequency, counted from its formulas:
-    compensated Gram update 54 per off-diagonal entry and view, double-float exp 198 per
-    (view, layer), right-hand side 52 per (view, layer, channel), Cholesky update 52 per
-    (r, l, k) plus 60 per pivot and 14 per scaled entry, triangular solves 52 per entry and
-    channel in each direction."""
-    gram = (N * (N - 1) // 2) * K * 54
-    exps = N * K * 198
-    rhs = N * K * C * 52
-    chol = ((N ** 3 - N) // 6) * 52 + N * 60 + (N * (N - 1) // 2) * 14
-    solves = 2 * (N * (N - 1) // 2) * C * 52 + 2 * N * C * 14
-    return gram + exps + rhs + chol + solves
+def df_ops_per_frequency(K, N, C, moment=True):
+    """FP32 operations of the double-float solve at one frequency, counted from its formulas
+    (each term: operations per item x items):
+
+    - phase d (u.w) from exact pieces 60 and double-float exp 190, per (view, layer);
+    - A - 1: 13 per (view, layer); right-hand side 56 per (view, layer, channel);
+    - Gram, moment form (disparities on a grid up to rounding): z_j^m and the four moments
+      234 per (view, layer), 49 per view, assembly 125 per off-diagonal entry; direct form:
+      54 per (off-diagonal entry, view) plus the A - 1 sums 30 per (view, layer);
+    - sum of b: 20 per (view, channel); Cholesky 56 per (r, l, k) update, 70 per pivot,
+      14 per scaled entry; condition estimate 3 x 2 x 8 per entry; triangular solves 56 per
+      (entry, channel) in each direction plus 14 per (row, channel)."""
+    nk = N * K
+    offd = N * (N - 1) // 2
+    work = nk * (60 + 190) + nk * 13 + nk * C * 56
+    if moment:
+        work += nk * 234 + K * 49 + offd * 125
+    else:
+        work += offd * K * 54 + nk * 30
+    work += K * C * 20 + N * C * 40
+    work += ((N ** 3 - N) // 6) * 56 + N * 70 + offd * 14
+    work += 3 * 2 * offd * 8
+    work += 2 * offd * C * 56 + 2 * N * C * 14
+    return work
 
 
-def roofline_entry(legs, clk):
+def moment_form_applies(u, d):
+    """The device-side test of the solve: 2 pi (spread of d about its grid) max|u| / sqrt(2) <= 1e-4."""
+    d = np.asarray(d, np.float64)
+    n = len(d)
+    delta = float(np.float32((np.float32(d[-1]) - np.float32(d[0])) / np.float32(n - 1))) if n > 1 else 0.0
+    e = d - d[0] - np.arange(n) * delta
+    umax = float(np.max(np.hypot(u[:, 0], u[:, 1])))
+    return 2 * np.pi * (e.max() - e.min()) * umax / np.sqrt(2) <= 1e-4
+
+
+# Algorithmic flops per frequency of an FP32 solve with a Toeplitz Gram (9x9 views, N = 30, RGB):
+# Gram 14.6k, A 14.6k, right-hand side 58.3k, Cholesky 36k, solves 21.6k.
+SURVEY_FLOPS_PER_FREQUENCY = 145_000
+
+
+def roofline_entry(legs, clk, moment):
     """The dominant kernel is the double-float solve (launch list); it is bound by the FP32 pipe."""
-    ops = df_ops_per_frequency(81, N, C) * q_half()
+    per_q = df_ops_per_frequency((2 * GRID + 1) ** 2, N, C, moment)
     ms = legs["solve_df_all_ms"]
-    achieved = ops / (ms / 1e3) / 1e12
+    achieved = per_q * q_half() / (ms / 1e3) / 1e12
     mhz = clk.get("sm_mhz") or 2070.0
     peak = 152 * 128 * mhz * 1e6 / 1e12  # one FP32 operation per lane per cycle
-    return {"kernel": "k_solve_df (double-float per-frequency solve, all 131,584 frequencies)", "bound": "alu",
-            "achieved": achieved, "peak": peak, "unit": "TFP32op/s", "frac": achieved / peak, "traffic": None,
+    form = "moment-form Gram" if moment else "direct Gram"
+    return {"kernel": f"k_solve_df (double-float per-frequency solve, {form}, all 131,584 frequencies)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFP32op/s", "frac": achieved / peak,
+            "traffic": None,
             "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock sampled in the run)",
-            "work_per_frequency_fp32_ops": df_ops_per_frequency(81, N, C)}
+            "work_per_frequency_fp32_ops": per_q,
+            "fp32_method_flops_per_frequency": SURVEY_FLOPS_PER_FREQUENCY,
+            "fp32_method_tflops": SURVEY_FLOPS_PER_FREQUENCY * q_half() / (ms / 1e3) / 1e12}
 
 
 if __name__ == "__main__":

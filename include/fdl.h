@@ -161,7 +161,7 @@ FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W,
  * and hosts (plugins, renderers, frameworks with their own caching allocator)
  * that own the whole device-memory budget and forbid allocations by libraries.
  * The paper has no counterpart: this is an integration variant only.
- * Its scratch is a fixed array inside the library (8,454,400 bytes on every
+ * Its scratch is a fixed array inside the library (8,455,168 bytes on every
  * GPU that loads it, held until the process exits); H * (W/2 + 1) must not
  * exceed 525,312 (a 1024 x 1024 image), otherwise FDL_ENOMEM.  The first call
  * on each device looks up the array's device address, so make it before any

@@ -50,6 +50,7 @@ struct FitWs {
   int* counters;
   float4* exp_table;
   float4* fft_tables;
+  float2* mom;  // kMomSlots: disparity grid deviations for the moment-form Gram
   int* flagged;
   int* flagged64;
   float* err;
@@ -66,6 +67,7 @@ FitWs carve_fit(void* ws, int K, int C, int H, int W, bool with_spectra) {
   f.counters = cv.take<int>(16);
   f.exp_table = cv.take<float4>(1024);
   f.fft_tables = cv.take<float4>((size_t)H + W);
+  f.mom = cv.take<float2>(kMomSlots);
   f.flagged = cv.take<int>((size_t)H * (W / 2 + 1));
   f.flagged64 = cv.take<int>((size_t)H * (W / 2 + 1));
   f.err = cv.take<float>((size_t)H * (W / 2 + 1));
@@ -120,9 +122,11 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
   const double budget32 = o->f32_error_budget > 0.0 ? o->f32_error_budget : 2e-6;
   p.counters = f.counters;
   p.exp_table = f.exp_table;
+  p.mom = f.mom;
   cudaError_t e = cudaMemsetAsync(f.counters, 0, 16 * sizeof(int), st);
   if (e != cudaSuccess) return FDL_ECUDA;
   e = launch_exp_table(f.exp_table, st);
+  if (e == cudaSuccess && p.mom != nullptr) e = launch_mom_check(p, st);
   if (e != cudaSuccess) return FDL_ECUDA;
   // Each tier records an error scale per frequency (condition estimate x solution
   // norm); the frequencies with the largest estimated errors are re-solved in the next
@@ -401,16 +405,17 @@ FDL_API int fdl_calib_grad(const float* spectra, int K, int C, int H, int W, con
 // ------------------------------------------------------------------ fixed-scratch fit
 // Scratch of fdl_fit_spectra_noalloc: a file-scope device array, so that the
 // entry point never allocates.  Every GPU that loads the library holds it
-// (8,454,400 bytes) until the process exits; all calls on a device share it.
+// (8,455,168 bytes) until the process exits; all calls on a device share it.
 namespace {
 
 constexpr size_t kNoAllocMaxBins = 1024 * 513;  // H * (W/2 + 1) of a 1024 x 1024 image
-constexpr size_t kNoAllocCounters = 256;
+constexpr size_t kNoAllocCounters = 1024;  // counters (64 B), then the kMomSlots float2 at 256
 constexpr size_t kNoAllocTable = 1024 * sizeof(float4);
 constexpr size_t kNoAllocSelect = 32768;  // >= select_scratch_bytes()
 constexpr size_t kNoAllocBytes =
     kNoAllocCounters + kNoAllocTable + kNoAllocSelect + 4 * kNoAllocMaxBins * sizeof(int);
 
+static_assert(256 + kMomSlots * sizeof(float2) <= kNoAllocCounters, "moment slots overlap the exp table");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -449,6 +454,7 @@ extern "C" FDL_API int fdl_fit_spectra_noalloc(const float* spectra, int K, int 
   char* b = static_cast<char*>(base);
   FitWs f;
   f.counters = reinterpret_cast<int*>(b);
+  f.mom = reinterpret_cast<float2*>(b + 256);
   f.exp_table = reinterpret_cast<float4*>(b + kNoAllocCounters);
   f.select = b + kNoAllocCounters + kNoAllocTable;
   f.flagged = reinterpret_cast<int*>(b + kNoAllocCounters + kNoAllocTable + kNoAllocSelect);

@@ -59,7 +59,12 @@ struct SolveParams {
   int* counters;       // [0] FP32 bins, [1] double-float bins, [2] breakdowns, [3] non-finite,
                        // [4] double-float list length, [5] FP64 list length, [6] FP64 bins
   const float4* exp_table;  // df table of exp(2 pi i n / 1024), n in [0, 1024)
+  // Moment form of the double-float Gram (nullable): kMomSlots float2, entries [0, N)
+  // e_k = d_k - d_0 - k Delta as double-floats, written by the check kernel, which also
+  // sets counters[8] to 1 when the moment form applies.
+  float2* mom;
 };
+constexpr int kMomSlots = 65;
 // FP32 solve of every stored bin; with estimate, also err / xn2 per bin (err = +inf
 // where the result is not trusted) and every bin counted in counters[0].
 cudaError_t launch_solve_f32(const SolveParams& p, bool estimate, cudaStream_t st);
@@ -71,6 +76,10 @@ cudaError_t launch_exp_table(float4* table, cudaStream_t st);
 // Double-float solve with the matrix in registers (N <= 48); same contract as
 // launch_solve_hp with f64 = false.
 bool solve_df_supported(int N);
+// Decides whether the disparities are close enough to a grid for the moment form of the
+// Gram matrix (counters[8]) and writes their deviations e_k to p.mom; must precede the
+// FP32 and double-float launches of a solve that sets p.mom.
+cudaError_t launch_mom_check(const SolveParams& p, cudaStream_t st);
 cudaError_t launch_solve_df(const SolveParams& p, bool all_bins, cudaStream_t st);
 
 // ---- tier selection (select.cu) ---------------------------------------------

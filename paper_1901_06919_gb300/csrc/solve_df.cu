@@ -12,6 +12,20 @@
 //    rounding error, plus the hi*lo cross terms, in the low word;
 //  * Cholesky runs on the register slots with the pivot column broadcast
 //    through shared memory; the triangular solves run one row per lane.
+//
+// Moment form of the Gram matrix (MOM = true).  G_rl = sum_j exp(2 pi i (d_l - d_r)
+// theta_j) depends on the pair only through d_l - d_r.  Writing d_k = d_0 + k Delta + e_k
+// (Delta = (d_{N-1} - d_0)/(N-1), e_k the deviation from an exact grid) and m = r - l,
+//   G_rl = sum_p (2 pi i eps)^p / p! conj(M_p(m)),  eps = e_l - e_r,
+//   M_p(m) = sum_j theta_j^p z_j^m,  z_j^m = exp(2 pi i m Delta theta_j)
+//          = A_jm conj(A_j0) exp(-2 pi i e_m theta_j),
+// an exact identity with the exponential of the small phase expanded to p <= 3.  Per
+// view that is N moments (lane m) instead of N(N+1)/2 products.  It applies when
+// x = 2 pi max|eps| max|theta| <= kMomXLim, so that the first omitted term, x^4/24,
+// is below 1e-17 (float32 linspace disparities: x ~ 5e-6 for |u| <= 4); k_mom_check
+// decides that on the device and exactly one of the two kernels does the work.
+// Precision: M_0 in double-float as K + sum (z - 1); M_1 in double-float (its term is
+// ~1e-5 of G); M_2, M_3 in FP32 (terms below 1e-11 and 1e-17 of G).
 #include "hp_solve.cuh"
 
 namespace fdl {
@@ -121,7 +135,60 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
                      __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
-template <int NMAX, int S>
+constexpr float kMomXLim = 1e-4f;
+
+// One warp: Delta, e_k for k < N (double-float, exact), and the flag counters[8] = 1
+// when 2 pi (max e - min e) (max_j |u_j| / sqrt(2)) <= kMomXLim (|w| <= 1/sqrt(2)).
+__global__ void k_mom_check(const float* __restrict__ d, int N, const float* __restrict__ u, int K, float2* mom,
+                            int* counters) {
+  const int lane = threadIdx.x;
+  const float d0 = d[0];
+  const float delta = N > 1 ? (d[N - 1] - d0) / (float)(N - 1) : 0.f;
+  float emin = INFINITY, emax = -INFINITY;
+  bool finite = true;
+  for (int k = lane; k < N; k += 32) {
+    const float dk = d[k];
+    finite = finite && isfinite(dk);
+    const df e = df_sub(two_sum(dk, -d0), two_prod((float)k, delta));
+    mom[k] = make_float2(e.hi, e.lo);
+    emin = fminf(emin, e.hi);
+    emax = fmaxf(emax, e.hi);
+  }
+  float umax = 0.f;
+  for (int j = lane; j < K; j += 32) {
+    const float ux = u[2 * j], uy = u[2 * j + 1];
+    finite = finite && isfinite(ux) && isfinite(uy);
+    umax = fmaxf(umax, sqrtf(ux * ux + uy * uy));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+  }
+  const bool all_finite = __all_sync(0xffffffffu, finite);
+  if (lane == 0) {
+    // relative slack for the low words of e, which max/min of the high words ignore
+    const float x = 6.2831853f * (emax - emin) * 1.0001f * umax * 0.70710678f + 1e-30f;
+    counters[8] = (all_finite && N <= 64 && x <= kMomXLim) ? 1 : 0;
+  }
+}
+
+// a + b with the "sloppy" double-word addition (error ~2^-46 (|a| + |b|)): used where
+// the absolute error is what matters (terms of magnitude <= 2)
+__device__ __forceinline__ df sadd_df(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// acc += v for double-float accumulators whose terms stay small (TwoSum on the high
+// words, low words added)
+__device__ __forceinline__ void acc_df(df& acc, df v) {
+  const df s = two_sum(acc.hi, v.hi);
+  acc = two_sum(s.hi, __fadd_rn(__fadd_rn(acc.lo, s.lo), v.lo));
+}
+
+template <int NMAX, int S, bool MOM>
 __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(SolveParams p, int all_bins) {
   constexpr int R = (NMAX + 31) / 32;  // rows per lane in the solves
   extern __shared__ float4 sm4[];
@@ -151,8 +218,16 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
 #define SR(s) (rl[s] >> 8)
 #define SL(s) (rl[s] & 255)
 #define SLOT_USED(s) (lane + 32 * (s) < E)
+  if (p.mom != nullptr) {
+    // exactly one of the moment and the general kernel runs (k_mom_check decided)
+    const bool mom_on = *((volatile int*)(p.counters + 8)) == 1;
+    if (mom_on != MOM) return;
+  }
   for (int i = lane; i < 2 * NMAX + 1; i += 32) Arow[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
+  float2 em[R];  // e_m of this lane's moments (moment form)
+#pragma unroll
+  for (int h = 0; h < R; ++h) em[h] = (MOM && lane + 32 * h < N) ? p.mom[lane + 32 * h] : make_float2(0.f, 0.f);
   const float4* tab = p.exp_table;
   const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(p.counters + 4));
   int nhp = 0, nbad = 0;
@@ -178,6 +253,19 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     dfc Ssum[R];  // S_r = sum_j (A_jr - 1)
 #pragma unroll
     for (int h = 0; h < R; ++h) Ssum[h] = {{0.f, 0.f}, {0.f, 0.f}};
+    // moment form: M0 = sum (z - 1), M1 = sum theta (z - 1) (double-float), M2, M3 = sum
+    // theta^2,3 (z - 1) (FP32), and the plain sums of theta^p (identical in every lane)
+    dfc M0[R], M1[R];
+    float2 M2[R], M3[R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+      M0[h] = {{0.f, 0.f}, {0.f, 0.f}};
+      M1[h] = {{0.f, 0.f}, {0.f, 0.f}};
+      M2[h] = make_float2(0.f, 0.f);
+      M3[h] = make_float2(0.f, 0.f);
+    }
+    df T1 = {0.f, 0.f};
+    float T2 = 0.f, T3 = 0.f;
 
     for (int j = 0; j < K; ++j) {
       const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
@@ -195,7 +283,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
           const df am = two_sum(t.hi, __fadd_rn(t.lo, a.re.v.lo));
           const float4 av = make_float4(am.hi, a.im.v.hi, am.lo, a.im.v.lo);
           Arow[r] = av;
-          {
+          if constexpr (!MOM) {
             const df s1 = two_sum(Ssum[h].re.hi, am.hi);
             Ssum[h].re = two_sum(s1.hi, __fadd_rn(__fadd_rn(Ssum[h].re.lo, s1.lo), am.lo));
             const df s2 = two_sum(Ssum[h].im.hi, a.im.v.hi);
@@ -205,6 +293,51 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
           for (int c = 0; c < 4; ++c)
             if (c < C) rhs_acc(y[h][c], av, bj[c]);
         }
+      }
+      if constexpr (MOM) {
+        // A_j0 (not A_j0 - 1) from lane 0, then z_j^m = A_jm conj(A_j0) exp(-2 pi i e_m theta_j)
+        // for this lane's m, and the moments of z - 1
+        const df theta = df_add(two_sum(th.p1, th.p2), df_from(__fadd_rn(th.e1, th.e2)));
+        const float th2 = theta.hi * theta.hi, th3 = th2 * theta.hi;
+        acc_df(T1, theta);
+        T2 += th2;
+        T3 += th3;
+        const dfc a0m = unpack(shfl4(lane == 0 ? Arow[0] : make_float4(0.f, 0.f, 0.f, 0.f), 0));
+        const dfc a0 = {df_add_f(a0m.re, 1.f), a0m.im};
+        const df twopi = {6.28318548202514648f, -1.74845553146951720e-07f};
+#pragma unroll
+        for (int h = 0; h < R; ++h) {
+          const int m = lane + 32 * h;
+          if (m < N) {
+            const float4 amv = Arow[m];
+            const dfc am = {df_add_f({amv.x, amv.z}, 1.f), {amv.y, amv.w}};
+            // w = A_jm conj(A_j0)
+            const dfc w = {sadd_df(df_mul(am.re, a0.re), df_mul(am.im, a0.im)),
+                           sadd_df(df_mul(am.im, a0.re), df_neg(df_mul(am.re, a0.im)))};
+            // z = w (cos phi + i sin phi), phi = -2 pi e_m theta, |phi| <= kMomXLim:
+            // cos phi = 1 - phi^2/2, sin phi = phi - phi^3/6 (next terms below 1e-17)
+            const df phi = df_neg(df_mul(df_mul({em[h].x, em[h].y}, theta), twopi));
+            const float hp2 = -0.5f * phi.hi * phi.hi;
+            const df sn = sadd_df(phi, df_from(phi.hi * hp2 * (1.f / 3.f)));
+            const df zr = sadd_df(w.re, df_from(w.re.hi * hp2));
+            const df zi = sadd_df(w.im, df_from(w.im.hi * hp2));
+            const dfc z = {sadd_df(zr, df_neg(df_mul(w.im, sn))), sadd_df(zi, df_mul(w.re, sn))};
+            // z - 1 (exact subtraction of the high word)
+            const df t = two_sum(z.re.hi, -1.f);
+            const df zm1r = two_sum(t.hi, __fadd_rn(t.lo, z.re.lo));
+            const df zm1i = z.im;
+            acc_df(M0[h].re, zm1r);
+            acc_df(M0[h].im, zm1i);
+            acc_df(M1[h].re, df_mul(theta, zm1r));
+            acc_df(M1[h].im, df_mul(theta, zm1i));
+            M2[h].x = fmaf(th2, zm1r.hi, M2[h].x);
+            M2[h].y = fmaf(th2, zm1i.hi, M2[h].y);
+            M3[h].x = fmaf(th3, zm1r.hi, M3[h].x);
+            M3[h].y = fmaf(th3, zm1i.hi, M3[h].y);
+          }
+        }
+        __syncwarp();
+        continue;
       }
       __syncwarp();
       // every slot, without a branch, so that the independent slot updates interleave;
@@ -225,20 +358,64 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     // frequencies every A_jk is close to 1 and the sums over a~ stay small, so
     // their rounding does not grow with the number of views the way the
     // running sums of nearly equal terms of A*A and A*b would.
-#pragma unroll
-    for (int h = 0; h < R; ++h)
-      if (lane + 32 * h < N) col[lane + 32 * h] = pack(Ssum[h]);
-    __syncwarp();
     const df Kdf = {(float)K, 0.f};
+    if constexpr (MOM) {
+      // moments to shared memory (the Ls region is free until after the factorisation):
+      // per m, [M0 | M1 (with sum theta added) | M2, M3 (with sums of theta^2,3 added)]
+      float4* Mm = Ls;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      renorm(G[s]);
-      if (SR(s) == SL(s)) {
-        G[s] = {Kdf, {0.f, 0.f}};  // sum_j |A_jk|^2 = K exactly
-      } else {
-        const dfc sr = unpack(col[SR(s)]), sl = unpack(col[SL(s)]);
-        G[s].re = df_add(G[s].re, df_add(Kdf, df_add(sr.re, sl.re)));
-        G[s].im = df_add(G[s].im, df_sub(sl.im, sr.im));
+      for (int h = 0; h < R; ++h) {
+        const int m = lane + 32 * h;
+        if (m < N) {
+          Mm[3 * m] = pack(M0[h]);
+          const dfc m1 = {df_add(M1[h].re, T1), M1[h].im};
+          Mm[3 * m + 1] = pack(m1);
+          Mm[3 * m + 2] = make_float4(M2[h].x + T2, M2[h].y, M3[h].x + T3, M3[h].y);
+        }
+      }
+      __syncwarp();
+      const df twopi = {6.28318548202514648f, -1.74845553146951720e-07f};
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int r = SR(s), l = SL(s);
+        if (r == l) {
+          G[s] = {Kdf, {0.f, 0.f}};  // sum_j |A_jk|^2 = K exactly (also unused slots)
+        } else {
+          const int m = r - l;
+          const float2 er = p.mom[r], el = p.mom[l];
+          const df eps = df_sub({el.x, el.y}, {er.x, er.y});
+          const df te = df_mul(eps, twopi);  // 2 pi eps
+          const dfc m0 = unpack(Mm[3 * m]), m1 = unpack(Mm[3 * m + 1]);
+          const float4 m23 = Mm[3 * m + 2];
+          // p = 0: K + conj(M0); p = 1: (2 pi i eps) conj(M1) = 2 pi eps (M1.im + i M1.re)
+          dfc g = {df_add(Kdf, m0.re), df_neg(m0.im)};
+          g.re = df_add(g.re, df_mul(te, m1.im));
+          g.im = df_add(g.im, df_mul(te, m1.re));
+          // p = 2: -(2 pi eps)^2 / 2 conj(M2); p = 3: -(2 pi eps)^3 / 6 (M3.im + i M3.re)
+          const float t = te.hi, c2 = -0.5f * t * t, c3 = -t * t * t * (1.f / 6.f);
+          const float gr = fmaf(c2, m23.x, c3 * m23.w);
+          const float gi = fmaf(-c2, m23.y, c3 * m23.z);
+          g.re = df_add_f(g.re, gr);
+          g.im = df_add_f(g.im, gi);
+          G[s] = g;
+        }
+      }
+      __syncwarp();
+    } else {
+#pragma unroll
+      for (int h = 0; h < R; ++h)
+        if (lane + 32 * h < N) col[lane + 32 * h] = pack(Ssum[h]);
+      __syncwarp();
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        renorm(G[s]);
+        if (SR(s) == SL(s)) {
+          G[s] = {Kdf, {0.f, 0.f}};  // sum_j |A_jk|^2 = K exactly
+        } else {
+          const dfc sr = unpack(col[SR(s)]), sl = unpack(col[SL(s)]);
+          G[s].re = df_add(G[s].re, df_add(Kdf, df_add(sr.re, sl.re)));
+          G[s].im = df_add(G[s].im, df_sub(sl.im, sr.im));
+        }
       }
     }
     // sum_j b_j per channel: lanes over views, then a butterfly of double-float adds
@@ -504,22 +681,37 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
   }
 }
 
-template <int NMAX, int S>
-cudaError_t launch_df_n(const SolveParams& p, bool all_bins, cudaStream_t st) {
+template <int NMAX, int S, bool MOM>
+cudaError_t launch_df_v(const SolveParams& p, bool all_bins, cudaStream_t st) {
   const size_t per_warp = (size_t)(2 * NMAX + NMAX * (NMAX + 1) / 2 + NMAX) * sizeof(float4);
   const size_t smem = per_warp * kDfWarps;
-  cudaError_t e = set_smem((const void*)k_solve_df<NMAX, S>, smem);
+  cudaError_t e = set_smem((const void*)k_solve_df<NMAX, S, MOM>, smem);
   if (e != cudaSuccess) return e;
   // one frequency per warp for the largest possible list: short CTAs let
   // higher-priority streams interleave (CTAs past the list length exit at once)
   const int bins = p.H * (p.W / 2 + 1);
-  k_solve_df<NMAX, S><<<(bins + kDfWarps - 1) / kDfWarps, kDfWarps * 32, smem, st>>>(p, all_bins ? 1 : 0);
+  k_solve_df<NMAX, S, MOM><<<(bins + kDfWarps - 1) / kDfWarps, kDfWarps * 32, smem, st>>>(p, all_bins ? 1 : 0);
   return cudaGetLastError();
+}
+
+// With p.mom set (launch_mom_check has run): the moment-form kernel and the general
+// kernel, of which exactly one does the work (the other exits at once).
+template <int NMAX, int S>
+cudaError_t launch_df_n(const SolveParams& p, bool all_bins, cudaStream_t st) {
+  if (p.mom == nullptr) return launch_df_v<NMAX, S, false>(p, all_bins, st);
+  cudaError_t e = launch_df_v<NMAX, S, true>(p, all_bins, st);
+  if (e == cudaSuccess) e = launch_df_v<NMAX, S, false>(p, all_bins, st);
+  return e;
 }
 
 }  // namespace
 
 bool solve_df_supported(int N) { return N <= 48; }
+
+cudaError_t launch_mom_check(const SolveParams& p, cudaStream_t st) {
+  k_mom_check<<<1, 32, 0, st>>>(p.d, p.N, p.u, p.K, p.mom, p.counters);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_solve_df(const SolveParams& p, bool all_bins, cudaStream_t st) {
   // register slots per lane: ceil(NMAX (NMAX + 1) / 64)

@@ -173,3 +173,35 @@ def test_more_than_48_layers(fdl, precision):
     err = rel_l2(got, ref)
     assert err < TOL, err
     assert counts["breakdown"] == 0 and counts["high_precision"] == 32 * 17
+
+
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_many_views_wide_baseline(fdl, precision):
+    """19x19 views spanning u in [-9, 9]: large phases d (u . w) and long sums over views.
+
+    The sums over views of A*A and A*b at the low, worst-conditioned frequencies are where
+    the double-float solve loses accuracy first (on its own it lands near 3e-5 here); the
+    error budgets of the mixed path must still hold against the FP64 oracle.
+    """
+    u = view_grid(9)
+    d = np.linspace(-3, 3, 30).astype(np.float32)
+    views, _ = occluding_planes(7, 64, 64, 1, u)
+    ref = O.fit(views, u, d.astype(np.float64), lam=1e-2, eps=1e-4)
+    got, counts = _gpu_fit(fdl, views, u, d, 1e-2, precision=precision)
+    err = rel_l2(got, ref)
+    assert err < TOL, err
+    assert counts["fp32"] + counts["df"] + counts["fp64"] == 64 * 33
+
+
+@pytest.mark.parametrize("precision", ["mixed", "df"])
+def test_irregular_disparities_take_the_direct_gram(fdl, precision):
+    """Disparities far from any grid (seeded, sorted uniform draws): the double-float solve
+    must take its direct Gram form instead of the moment form and still meet the tolerance."""
+    u = view_grid(3)
+    d = np.sort(np.random.default_rng(4).uniform(-2.5, 2.5, 20)).astype(np.float32)
+    views, _ = occluding_planes(2, 64, 64, 3, u)
+    ref = O.fit(views, u, d.astype(np.float64), lam=1e-2, eps=1e-4)
+    got, counts = _gpu_fit(fdl, views, u, d, 1e-2, precision=precision)
+    err = rel_l2(got, ref)
+    assert err < TOL, err
+    assert counts["fp32"] + counts["df"] + counts["fp64"] == 64 * 33
