@@ -755,19 +755,20 @@ def df_ops_per_frequency(K, N, C, moment=True):
     """FP32 operations of the double-float solve at one frequency, counted from its formulas
     (each term: operations per item x items):
 
-    - phase d (u.w) from exact pieces 60 and double-float exp 190, per (view, layer);
+    - phase d (u.w) from exact pieces 49 and double-float exp 168, per (view, layer);
     - A - 1: 13 per (view, layer); right-hand side 56 per (view, layer, channel);
-    - Gram, moment form (disparities on a grid up to rounding): z_j^m and the four moments
-      234 per (view, layer), 49 per view, assembly 125 per off-diagonal entry; direct form:
-      54 per (off-diagonal entry, view) plus the A - 1 sums 30 per (view, layer);
+    - Gram, moment form (disparities on a grid up to rounding): w_jm = A_jm conj(A_j0) and
+      the four moments of w - 1 133 per (view, layer), 49 per view, assembly 145 per
+      off-diagonal entry; direct form: 54 per (off-diagonal entry, view) plus the A - 1
+      sums 30 per (view, layer);
     - sum of b: 20 per (view, channel); Cholesky 56 per (r, l, k) update, 70 per pivot,
       14 per scaled entry; condition estimate 3 x 2 x 8 per entry; triangular solves 56 per
       (entry, channel) in each direction plus 14 per (row, channel)."""
     nk = N * K
     offd = N * (N - 1) // 2
-    work = nk * (60 + 190) + nk * 13 + nk * C * 56
+    work = nk * (49 + 168) + nk * 13 + nk * C * 56
     if moment:
-        work += nk * 234 + K * 49 + offd * 125
+        work += nk * 133 + K * 49 + offd * 145
     else:
         work += offd * K * 54 + nk * 30
     work += K * C * 20 + N * C * 40

@@ -15,17 +15,17 @@
 //
 // Moment form of the Gram matrix (MOM = true).  G_rl = sum_j exp(2 pi i (d_l - d_r)
 // theta_j) depends on the pair only through d_l - d_r.  Writing d_k = d_0 + k Delta + e_k
-// (Delta = (d_{N-1} - d_0)/(N-1), e_k the deviation from an exact grid) and m = r - l,
-//   G_rl = sum_p (2 pi i eps)^p / p! conj(M_p(m)),  eps = e_l - e_r,
-//   M_p(m) = sum_j theta_j^p z_j^m,  z_j^m = exp(2 pi i m Delta theta_j)
-//          = A_jm conj(A_j0) exp(-2 pi i e_m theta_j),
-// an exact identity with the exponential of the small phase expanded to p <= 3.  Per
-// view that is N moments (lane m) instead of N(N+1)/2 products.  It applies when
-// x = 2 pi max|eps| max|theta| <= kMomXLim, so that the first omitted term, x^4/24,
-// is below 1e-17 (float32 linspace disparities: x ~ 5e-6 for |u| <= 4); k_mom_check
-// decides that on the device and exactly one of the two kernels does the work.
-// Precision: M_0 in double-float as K + sum (z - 1); M_1 in double-float (its term is
-// ~1e-5 of G); M_2, M_3 in FP32 (terms below 1e-11 and 1e-17 of G).
+// (Delta = (d_{N-1} - d_0)/(N-1), e_k the deviation from an exact grid, e_0 = 0),
+// w_jm = A_jm conj(A_j0) = exp(2 pi i (m Delta + e_m) theta_j) and m = r - l,
+//   conj(A_jr) A_jl = conj(w_jm) exp(2 pi i eta theta_j),  eta = e_l - e_r + e_m,
+//   G_rl = sum_s (2 pi i eta)^s / s! conj(W_s(m)),  W_s(m) = sum_j theta_j^s w_jm,
+// an exact identity with the exponential of the small phase expanded to s <= 3.  Per
+// view that is N moment sets (lane m) instead of N(N+1)/2 products.  It applies when
+// x = 2 pi max|e_l - e_r| max|theta| <= kMomXLim (then |2 pi eta theta| <= 2x and the
+// first omitted term, (2x)^4/24, is below 1e-17; float32 linspace disparities give
+// x ~ 5e-6 for |u| <= 4); k_mom_check decides that on the device and exactly one of the
+// two kernels does the work.  Precision: W_0 in double-float as K + sum (w - 1), W_1 in
+// double-float (its term is ~2x of G), W_2, W_3 in FP32 (terms below 2x^2 and 2x^3 of G).
 #include "hp_solve.cuh"
 
 namespace fdl {
@@ -33,9 +33,10 @@ namespace fdl {
 namespace {
 
 constexpr int kDfWarps = 4;
-#ifndef FDL_DF_MINBLOCKS
-#define FDL_DF_MINBLOCKS 2
-#endif
+// CTAs per SM the register allocation must allow, by NMAX: measured on the 512x512
+// light fields, all frequencies in double-float (N = 16: 7.8 / 6.2 / 5.7 ms with 2 / 3 / 4;
+// N = 30: 23.6 / 19.7 / 23.6 ms; N = 40: 41.5 / 66.3 / 69.5 ms, where spills dominate).
+constexpr int df_min_blocks(int nmax) { return nmax <= 16 ? 4 : (nmax <= 32 ? 3 : 2); }
 
 // entry (r, l), l <= r, numbered column-major: column l starts at l*N - l(l-1)/2
 __device__ __forceinline__ int col_start(int l, int N) { return l * N - (l * (l - 1)) / 2; }
@@ -135,7 +136,7 @@ __device__ __forceinline__ float4 shfl4(float4 v, int src) {
                      __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
-constexpr float kMomXLim = 1e-4f;
+constexpr float kMomXLim = 5e-5f;
 
 // One warp: Delta, e_k for k < N (double-float, exact), and the flag counters[8] = 1
 // when 2 pi (max e - min e) (max_j |u_j| / sqrt(2)) <= kMomXLim (|w| <= 1/sqrt(2)).
@@ -189,7 +190,7 @@ __device__ __forceinline__ void acc_df(df& acc, df v) {
 }
 
 template <int NMAX, int S, bool MOM>
-__global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(SolveParams p, int all_bins) {
+__global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df(SolveParams p, int all_bins) {
   constexpr int R = (NMAX + 31) / 32;  // rows per lane in the solves
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -253,8 +254,8 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
     dfc Ssum[R];  // S_r = sum_j (A_jr - 1)
 #pragma unroll
     for (int h = 0; h < R; ++h) Ssum[h] = {{0.f, 0.f}, {0.f, 0.f}};
-    // moment form: M0 = sum (z - 1), M1 = sum theta (z - 1) (double-float), M2, M3 = sum
-    // theta^2,3 (z - 1) (FP32), and the plain sums of theta^p (identical in every lane)
+    // moment form: M0 = sum (w - 1), M1 = sum theta (w - 1) (double-float), M2, M3 = sum
+    // theta^2,3 (w - 1) (FP32), and the plain sums of theta^p (identical in every lane)
     dfc M0[R], M1[R];
     float2 M2[R], M3[R];
 #pragma unroll
@@ -273,11 +274,14 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
       float2 bj[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) bj[c] = c < C ? *p.b.at((long long)j * C + c, ky, kx, M) : make_float2(0.f, 0.f);
+      dfc aR[R];  // A_jr of this lane's rows (moment form)
 #pragma unroll
       for (int h = 0; h < R; ++h) {
         const int r = lane + 32 * h;
+        aR[h] = {{0.f, 0.f}, {0.f, 0.f}};
         if (r < N) {
           const cx<Rdf> a = cexp2pi(phase_r(th, dr[h]), tab);
+          aR[h] = {a.re.v, a.im.v};
           // A - 1: the subtraction of the high word is exact (TwoSum)
           const df t = two_sum(a.re.v.hi, -1.f);
           const df am = two_sum(t.hi, __fadd_rn(t.lo, a.re.v.lo));
@@ -295,45 +299,30 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
         }
       }
       if constexpr (MOM) {
-        // A_j0 (not A_j0 - 1) from lane 0, then z_j^m = A_jm conj(A_j0) exp(-2 pi i e_m theta_j)
-        // for this lane's m, and the moments of z - 1
+        // w_jm = A_jm conj(A_j0) for this lane's m (A_j0 from lane 0) and the moments of w - 1
         const df theta = df_add(two_sum(th.p1, th.p2), df_from(__fadd_rn(th.e1, th.e2)));
         const float th2 = theta.hi * theta.hi, th3 = th2 * theta.hi;
         acc_df(T1, theta);
         T2 += th2;
         T3 += th3;
-        const dfc a0m = unpack(shfl4(lane == 0 ? Arow[0] : make_float4(0.f, 0.f, 0.f, 0.f), 0));
-        const dfc a0 = {df_add_f(a0m.re, 1.f), a0m.im};
-        const df twopi = {6.28318548202514648f, -1.74845553146951720e-07f};
+        const dfc a0 = unpack(shfl4(pack(aR[0]), 0));
 #pragma unroll
         for (int h = 0; h < R; ++h) {
-          const int m = lane + 32 * h;
-          if (m < N) {
-            const float4 amv = Arow[m];
-            const dfc am = {df_add_f({amv.x, amv.z}, 1.f), {amv.y, amv.w}};
-            // w = A_jm conj(A_j0)
-            const dfc w = {sadd_df(df_mul(am.re, a0.re), df_mul(am.im, a0.im)),
-                           sadd_df(df_mul(am.im, a0.re), df_neg(df_mul(am.re, a0.im)))};
-            // z = w (cos phi + i sin phi), phi = -2 pi e_m theta, |phi| <= kMomXLim:
-            // cos phi = 1 - phi^2/2, sin phi = phi - phi^3/6 (next terms below 1e-17)
-            const df phi = df_neg(df_mul(df_mul({em[h].x, em[h].y}, theta), twopi));
-            const float hp2 = -0.5f * phi.hi * phi.hi;
-            const df sn = sadd_df(phi, df_from(phi.hi * hp2 * (1.f / 3.f)));
-            const df zr = sadd_df(w.re, df_from(w.re.hi * hp2));
-            const df zi = sadd_df(w.im, df_from(w.im.hi * hp2));
-            const dfc z = {sadd_df(zr, df_neg(df_mul(w.im, sn))), sadd_df(zi, df_mul(w.re, sn))};
-            // z - 1 (exact subtraction of the high word)
-            const df t = two_sum(z.re.hi, -1.f);
-            const df zm1r = two_sum(t.hi, __fadd_rn(t.lo, z.re.lo));
-            const df zm1i = z.im;
-            acc_df(M0[h].re, zm1r);
-            acc_df(M0[h].im, zm1i);
-            acc_df(M1[h].re, df_mul(theta, zm1r));
-            acc_df(M1[h].im, df_mul(theta, zm1i));
-            M2[h].x = fmaf(th2, zm1r.hi, M2[h].x);
-            M2[h].y = fmaf(th2, zm1i.hi, M2[h].y);
-            M3[h].x = fmaf(th3, zm1r.hi, M3[h].x);
-            M3[h].y = fmaf(th3, zm1i.hi, M3[h].y);
+          if (lane + 32 * h < N) {
+            const dfc& am = aR[h];
+            const df wr = sadd_df(df_mul(am.re, a0.re), df_mul(am.im, a0.im));
+            const df wi = sadd_df(df_mul(am.im, a0.re), df_neg(df_mul(am.re, a0.im)));
+            // w - 1 (exact subtraction of the high word)
+            const df t = two_sum(wr.hi, -1.f);
+            const df wm1r = two_sum(t.hi, __fadd_rn(t.lo, wr.lo));
+            acc_df(M0[h].re, wm1r);
+            acc_df(M0[h].im, wi);
+            acc_df(M1[h].re, df_mul(theta, wm1r));
+            acc_df(M1[h].im, df_mul(theta, wi));
+            M2[h].x = fmaf(th2, wm1r.hi, M2[h].x);
+            M2[h].y = fmaf(th2, wi.hi, M2[h].y);
+            M3[h].x = fmaf(th3, wm1r.hi, M3[h].x);
+            M3[h].y = fmaf(th3, wi.hi, M3[h].y);
           }
         }
         __syncwarp();
@@ -382,16 +371,16 @@ __global__ void __launch_bounds__(kDfWarps * 32, FDL_DF_MINBLOCKS) k_solve_df(So
           G[s] = {Kdf, {0.f, 0.f}};  // sum_j |A_jk|^2 = K exactly (also unused slots)
         } else {
           const int m = r - l;
-          const float2 er = p.mom[r], el = p.mom[l];
-          const df eps = df_sub({el.x, el.y}, {er.x, er.y});
-          const df te = df_mul(eps, twopi);  // 2 pi eps
+          const float2 er = p.mom[r], el = p.mom[l], emm = p.mom[m];
+          const df eta = df_add(df_sub({el.x, el.y}, {er.x, er.y}), {emm.x, emm.y});
+          const df te = df_mul(eta, twopi);  // 2 pi eta
           const dfc m0 = unpack(Mm[3 * m]), m1 = unpack(Mm[3 * m + 1]);
           const float4 m23 = Mm[3 * m + 2];
-          // p = 0: K + conj(M0); p = 1: (2 pi i eps) conj(M1) = 2 pi eps (M1.im + i M1.re)
+          // s = 0: K + conj(W0); s = 1: (2 pi i eta) conj(W1) = 2 pi eta (W1.im + i W1.re)
           dfc g = {df_add(Kdf, m0.re), df_neg(m0.im)};
           g.re = df_add(g.re, df_mul(te, m1.im));
           g.im = df_add(g.im, df_mul(te, m1.re));
-          // p = 2: -(2 pi eps)^2 / 2 conj(M2); p = 3: -(2 pi eps)^3 / 6 (M3.im + i M3.re)
+          // s = 2: -(2 pi eta)^2 / 2 conj(W2); s = 3: -(2 pi eta)^3 / 6 (W3.im + i W3.re)
           const float t = te.hi, c2 = -0.5f * t * t, c3 = -t * t * t * (1.f / 6.f);
           const float gr = fmaf(c2, m23.x, c3 * m23.w);
           const float gi = fmaf(-c2, m23.y, c3 * m23.z);
