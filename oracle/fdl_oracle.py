@@ -70,9 +70,29 @@ def fft_radix2(x, axis: int = -1, inverse: bool = False) -> np.ndarray:
     return np.moveaxis(x, -1, axis)
 
 
+def dft_direct(x, axis: int = -1, inverse: bool = False) -> np.ndarray:
+    """DFT along ``axis`` by its definition, for any length: the product with the matrix
+    ``F[k, n] = exp(-/+ 2 pi i (k n mod len) / len)`` (``inverse=True`` takes ``+``).  No
+    normalisation.  ``k n`` is reduced modulo the length in integers before the exponential."""
+    x = np.moveaxis(np.asarray(x, dtype=np.complex128), axis, -1)
+    n = x.shape[-1]
+    kn = np.outer(np.arange(n), np.arange(n)) % n
+    sign = 1.0 if inverse else -1.0
+    F = np.exp(sign * 2j * np.pi * kn / n)
+    return np.moveaxis(x @ F.T, -1, axis)
+
+
+def dft_1d(x, axis: int = -1, inverse: bool = False) -> np.ndarray:
+    """The radix-2 DFT for power-of-two lengths, the definition otherwise."""
+    n = np.shape(x)[axis]
+    if n & (n - 1) == 0:
+        return fft_radix2(x, axis=axis, inverse=inverse)
+    return dft_direct(x, axis=axis, inverse=inverse)
+
+
 def dft2(img) -> np.ndarray:
     """Full 2D forward DFT over the last two axes."""
-    return fft_radix2(fft_radix2(img, axis=-1), axis=-2)
+    return dft_1d(dft_1d(img, axis=-1), axis=-2)
 
 
 def half_spectrum(img) -> np.ndarray:
@@ -109,7 +129,7 @@ def image_from_half(S: np.ndarray, W: int) -> np.ndarray:
     """Real image: Re(inverse DFT of the completed spectrum) / (H W)."""
     H = S.shape[-2]
     full = complete_half(S, W)
-    z = fft_radix2(fft_radix2(full, axis=-1, inverse=True), axis=-2, inverse=True)
+    z = dft_1d(dft_1d(full, axis=-1, inverse=True), axis=-2, inverse=True)
     return np.real(z) / (H * W)
 
 
@@ -213,11 +233,21 @@ def solve_bins(b, u, d, wy, wx, lam: float, eps: float, reg: int = REG_VIEW2):
     return gauss_solve(G, y)
 
 
+def full_width(Wh: int, W=None) -> int:
+    """Image width of a stored half of ``Wh = W//2 + 1`` columns: ``W`` when given (an odd
+    width cannot be told from ``Wh``), else the even width ``2 (Wh - 1)``."""
+    if W is None:
+        return 2 * (Wh - 1)
+    if W // 2 + 1 != Wh:
+        raise ValueError("W does not match the stored half")
+    return int(W)
+
+
 def fit_spectra(b_half, u, d, lam: float, eps: float = 1e-4, reg: int = REG_VIEW2,
-                chunk: int = 2048) -> np.ndarray:
+                chunk: int = 2048, W=None) -> np.ndarray:
     """Layer spectra ``[N][C][H][W/2+1]`` from input half spectra ``[K][C][H][W/2+1]``."""
     K, C, H, Wh = b_half.shape
-    W = 2 * (Wh - 1)
+    W = full_width(Wh, W)
     wy, wx = half_grid(H, W)
     bq = np.moveaxis(b_half.reshape(K, C, H * Wh), -1, 0)  # [q, K, C]
     N = len(d)
@@ -230,7 +260,8 @@ def fit_spectra(b_half, u, d, lam: float, eps: float = 1e-4, reg: int = REG_VIEW
 
 def fit(views, u, d, lam: float, eps: float = 1e-4, reg: int = REG_VIEW2) -> np.ndarray:
     """Layer construction of Sec. V-A: DFT of every view, then one solve per bin."""
-    return fit_spectra(half_spectrum(np.asarray(views, np.float64)), u, d, lam, eps, reg)
+    views = np.asarray(views, np.float64)
+    return fit_spectra(half_spectrum(views), u, d, lam, eps, reg, W=views.shape[-1])
 
 
 # ----------------------------------------------------------------------------
@@ -264,13 +295,13 @@ def aperture_ft(kind: int, radius: float, nu_y, nu_x, points=None) -> np.ndarray
 
 
 def render_spectrum(layers, d, u0, s: float, kind: int = AP_PINHOLE, radius: float = 0.0,
-                    points=None) -> np.ndarray:
+                    points=None, W=None) -> np.ndarray:
     """Half spectrum of the image ``B^s_{u0}``:
 
     ``sum_k exp(+2 pi i d_k (u0 . w)) psi_hat((s - d_k) w) L^k(w)`` (Eq. BsFourier).
     """
     N, C, H, Wh = layers.shape
-    W = 2 * (Wh - 1)
+    W = full_width(Wh, W)
     wy, wx = half_grid(H, W)
     wy = wy.reshape(H, Wh)
     wx = wx.reshape(H, Wh)
@@ -284,10 +315,10 @@ def render_spectrum(layers, d, u0, s: float, kind: int = AP_PINHOLE, radius: flo
 
 
 def render(layers, d, u0, s: float = 0.0, kind: int = AP_PINHOLE, radius: float = 0.0,
-           points=None) -> np.ndarray:
+           points=None, W=None) -> np.ndarray:
     """Rendered image ``[C][H][W]`` (Sec. VI-A: Eq. BsFourier, then the inverse DFT)."""
-    W = 2 * (layers.shape[-1] - 1)
-    return image_from_half(render_spectrum(layers, d, u0, s, kind, radius, points), W)
+    W = full_width(layers.shape[-1], W)
+    return image_from_half(render_spectrum(layers, d, u0, s, kind, radius, points, W), W)
 
 
 def shift_and_sum(layers_spatial, d, u0, s, points) -> np.ndarray:

@@ -110,3 +110,44 @@ def test_dft_at_bins_is_the_definition():
     ref = np.fft.fft2(img)[:, ky, kx]
     assert np.allclose(O.dft_at_bins(img, ky, kx), ref, atol=1e-11)
     assert np.allclose(O.dft_at_bins(img, ky, kx), O.dft2(img)[:, ky, kx], atol=1e-11)
+
+
+# ---- lengths that are not powers of two (the paper's 625 x 434, 379 x 379, 1920 x 1080)
+
+@pytest.mark.parametrize("n", [3, 5, 6, 7, 12, 31, 60])
+def test_direct_dft_matches_bruteforce(n):
+    rng = np.random.default_rng(100 + n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for inv in (False, True):
+        got = O.dft_direct(x, inverse=inv)
+        ref = naive_dft(x, inverse=inv)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_direct_dft_matches_library_fft_on_paper_lengths():
+    rng = np.random.default_rng(7)
+    for n in (379, 434, 625):
+        x = rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))
+        assert np.allclose(O.dft_1d(x), np.fft.fft(x), rtol=0, atol=1e-9)
+        assert np.allclose(O.dft_1d(x, inverse=True), np.fft.ifft(x) * n, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("shape", [(15, 21), (12, 20), (7, 16), (16, 9)])
+def test_half_spectrum_and_image_for_any_size(shape):
+    H, W = shape
+    rng = np.random.default_rng(H * 100 + W)
+    img = rng.random((2, H, W))
+    S = O.half_spectrum(img)
+    assert S.shape == (2, H, W // 2 + 1)
+    assert np.allclose(S, np.fft.rfft2(img), atol=1e-11)
+    assert np.allclose(O.image_from_half(S, W), img, atol=1e-12)
+    # a spectrum that is not Hermitian-consistent: numpy's C2R, which keeps the real
+    # part of the completed inverse, gives the same image
+    T = rng.standard_normal((H, W // 2 + 1)) + 1j * rng.standard_normal((H, W // 2 + 1))
+    assert np.allclose(O.image_from_half(T, W), np.fft.irfft2(T, s=(H, W)), atol=1e-12)
+
+
+def test_frequency_convention_odd_sizes():
+    assert np.allclose(O.freq_y(5), [0, 1 / 5, 2 / 5, -2 / 5, -1 / 5])
+    assert np.allclose(O.freq_x_half(5), [0, 1 / 5, 2 / 5])
+    assert np.allclose(O.freq_y(6), np.fft.fftfreq(6))

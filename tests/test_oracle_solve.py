@@ -111,10 +111,11 @@ def test_hermitian_symmetry_of_full_spectrum_solve():
     assert np.allclose(x_neg, np.conj(x_pos), atol=1e-13 * np.abs(x_pos).max())
 
 
-def test_layer_recovery_from_model_views():
+@pytest.mark.parametrize("H,W", [(32, 32), (27, 45), (30, 42)])
+def test_layer_recovery_from_model_views(H, W):
     """Views synthesised from N layers (K >= N, no noise) give the layers back as lambda -> 0
-    on every bin where A is well conditioned (Sec. V-A; scene model of Sec. IV-A)."""
-    H = W = 32
+    on every bin where A is well conditioned (Sec. V-A; scene model of Sec. IV-A), for
+    power-of-two and other sizes."""
     u = view_grid(1)
     d = np.linspace(-2, 2, 8)
     views, layers = layered_scene(7, H, W, 1, u, d, sigma=0.0)
