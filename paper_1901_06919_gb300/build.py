@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfdl.so")
-SOURCES = ["fft.cu", "fft_df.cu", "solve.cu", "solve_df.cu", "select.cu", "render.cu", "calib.cu", "api.cu"]
+SOURCES = ["fft.cu", "fft_df.cu", "fft_gen.cu", "solve.cu", "solve_df.cu", "select.cu", "render.cu", "calib.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

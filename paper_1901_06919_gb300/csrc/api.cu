@@ -29,7 +29,37 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
-bool shape_ok(int H, int W) { return pow2_in(H, 16, 4096) && pow2_in(W, 16, 4096); }
+bool pow2_shape(int H, int W) { return pow2_in(H, 16, 4096) && pow2_in(W, 16, 4096); }
+
+// Powers of two use the radix-4/2 DFT kernels and the split spectrum layout; other sizes
+// (16..4096, see gen_supported) the general-length kernels and the dense layout.
+bool shape_ok(int H, int W) {
+  if (pow2_shape(H, W)) return true;
+  return H >= 16 && W >= 16 && H <= 4096 && W <= 4096 && gen_supported(H) && gen_supported(W);
+}
+
+// Plans of the general-length DFTs, their tables one after the other (H first).
+struct GenPlans {
+  GenPlan ph, pw;
+  size_t elems;
+};
+GenPlans gen_plans(int H, int W) {
+  GenPlans g;
+  gen_plan(H, 0, &g.ph);
+  gen_plan(W, g.ph.elems, &g.pw);
+  g.elems = (size_t)g.ph.elems + g.pw.elems;
+  return g;
+}
+// float4 entries of DFT tables a forward transform of an H x W image needs
+size_t dft_table_elems(int H, int W) { return pow2_shape(H, W) ? (size_t)H + W : gen_plans(H, W).elems; }
+// ... and an inverse one (the power-of-two inverse kernels need none)
+size_t inv_table_elems(int H, int W) { return pow2_shape(H, W) ? 0 : gen_plans(H, W).elems; }
+
+cudaError_t launch_gen_tables2(const GenPlans& g, float4* tables, cudaStream_t st) {
+  cudaError_t e = launch_gen_tables(g.ph, tables, st);
+  if (e == cudaSuccess) e = launch_gen_tables(g.pw, tables, st);
+  return e;
+}
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? FDL_OK : FDL_ECUDA; }
 
@@ -66,7 +96,7 @@ FitWs carve_fit(void* ws, int K, int C, int H, int W, bool with_spectra) {
   FitWs f;
   f.counters = cv.take<int>(16);
   f.exp_table = cv.take<float4>(1024);
-  f.fft_tables = cv.take<float4>((size_t)H + W);
+  f.fft_tables = cv.take<float4>(dft_table_elems(H, W));
   f.mom = cv.take<float2>(kMomSlots);
   f.flagged = cv.take<int>((size_t)H * (W / 2 + 1));
   f.flagged64 = cv.take<int>((size_t)H * (W / 2 + 1));
@@ -184,7 +214,31 @@ size_t render_ws_bytes(int B, int C, int H, int W, bool with_reqs) {
   if (with_reqs) s += align_up((size_t)B * sizeof(fdl_request));
   s += align_up((size_t)B * C * H * (W / 2) * sizeof(float2));
   s += align_up((size_t)B * C * H * sizeof(float2));
+  s += align_up(inv_table_elems(H, W) * sizeof(float4));
   return s;
+}
+
+// Spectra of a render, then the inverse DFT into images: `main`/`nyq` carved in that
+// order (the dense layout of other sizes starts at `main` and fits in both), `tables`
+// after them.
+cudaError_t render_inverse(float2* main, float2* nyq, float4* tables, int B, int C, int H, int W, float* out,
+                           const fdl_request* req, const int* count, cudaStream_t st) {
+  const float scale = 1.f / ((float)H * (float)W);
+  if (pow2_shape(H, W)) {
+    cudaError_t e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, count, C, st);
+    if (e == cudaSuccess) e = launch_irfft_rows(main, out, (long long)B * C * H, H, W, scale, req, count, C, st);
+    return e;
+  }
+  const GenPlans g = gen_plans(H, W);
+  const SpecView sp = spec_dense(main, H, W);
+  cudaError_t e = launch_gen_tables2(g, tables, st);
+  if (e == cudaSuccess) e = launch_gen_cols(sp, sp, B * C, H, W, true, g.ph, tables, count, C, st);
+  if (e == cudaSuccess)
+    e = launch_gen_rows_inv(sp, out, (long long)B * C * H, H, W, scale, req, count, C, g.pw, tables, st);
+  return e;
+}
+SpecView render_spec_view(float2* main, float2* nyq, int H, int W) {
+  return pow2_shape(H, W) ? spec_split(main, nyq, H, W) : spec_dense(main, H, W);
 }
 
 }  // namespace
@@ -215,7 +269,7 @@ FDL_API int fdl_version(void) { return 1; }
 // ------------------------------------------------------------------ DFTs
 FDL_API size_t fdl_rfft2_workspace_size(int nimg, int H, int W) {
   if (nimg < 1 || !shape_ok(H, W)) return 0;
-  return spec_tmp_bytes(nimg, H, W) + align_up(fft_df_table_bytes(H, W));
+  return spec_tmp_bytes(nimg, H, W) + align_up(dft_table_elems(H, W) * sizeof(float4));
 }
 
 FDL_API int fdl_rfft2(const float* images, int nimg, int H, int W, float* spectra, void* workspace,
@@ -225,6 +279,14 @@ FDL_API int fdl_rfft2(const float* images, int nimg, int H, int W, float* spectr
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float2* tmp = static_cast<float2*>(workspace);
   float4* tables = reinterpret_cast<float4*>(static_cast<char*>(workspace) + spec_tmp_bytes(nimg, H, W));
+  if (!pow2_shape(H, W)) {
+    const GenPlans g = gen_plans(H, W);
+    const SpecView out = spec_dense(reinterpret_cast<float2*>(spectra), H, W);
+    cudaError_t e = launch_gen_tables2(g, tables, st);
+    if (e == cudaSuccess) e = launch_gen_rows_fwd(images, out, (long long)nimg * H, H, W, g.pw, tables, st);
+    if (e == cudaSuccess) e = launch_gen_cols(out, out, nimg, H, W, false, g.ph, tables, nullptr, 1, st);
+    return cuda_status(e);
+  }
   cudaError_t e = launch_twiddle_tables(tables, H, W, st);
   if (e == cudaSuccess) e = launch_rfft_rows_df(images, tmp, (long long)nimg * H, W, tables, st);
   if (e == cudaSuccess)
@@ -235,6 +297,8 @@ FDL_API int fdl_rfft2(const float* images, int nimg, int H, int W, float* spectr
 
 FDL_API size_t fdl_irfft2_workspace_size(int nimg, int H, int W) {
   if (nimg < 1 || !shape_ok(H, W)) return 0;
+  if (!pow2_shape(H, W))  // dense copy of the spectra, then the tables
+    return align_up((size_t)nimg * H * (W / 2 + 1) * sizeof(float2)) + align_up(inv_table_elems(H, W) * sizeof(float4));
   return spec_tmp_bytes(nimg, H, W);
 }
 
@@ -244,6 +308,19 @@ FDL_API int fdl_irfft2(const float* spectra, int nimg, int H, int W, float* imag
   if (workspace_bytes < fdl_irfft2_workspace_size(nimg, H, W)) return FDL_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float2* tmp = static_cast<float2*>(workspace);
+  if (!pow2_shape(H, W)) {
+    const GenPlans g = gen_plans(H, W);
+    float4* tables =
+        reinterpret_cast<float4*>(static_cast<char*>(workspace) + align_up((size_t)nimg * H * (W / 2 + 1) * sizeof(float2)));
+    const SpecView in = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
+    const SpecView t = spec_dense(tmp, H, W);
+    cudaError_t e = launch_gen_tables2(g, tables, st);
+    if (e == cudaSuccess) e = launch_gen_cols(in, t, nimg, H, W, true, g.ph, tables, nullptr, 1, st);
+    if (e == cudaSuccess)
+      e = launch_gen_rows_inv(t, images, (long long)nimg * H, H, W, 1.f / ((float)H * (float)W), nullptr, nullptr, 1,
+                              g.pw, tables, st);
+    return cuda_status(e);
+  }
   cudaError_t e = launch_fft_cols_inv(spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W),
                                       tmp, nimg, H, W, nullptr, 1, st);
   if (e == cudaSuccess)
@@ -267,6 +344,16 @@ FDL_API int fdl_fit(const float* views, int K, int C, int H, int W, const float*
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   FitWs f = carve_fit(workspace, K, C, H, W, true);
   const int nimg = K * C;
+  if (!pow2_shape(H, W)) {
+    // dense half spectra from spec_main (spec_main and spec_nyq are carved back to back)
+    const GenPlans g = gen_plans(H, W);
+    const SpecView b = spec_dense(f.spec_main, H, W);
+    cudaError_t e = launch_gen_tables2(g, f.fft_tables, st);
+    if (e == cudaSuccess) e = launch_gen_rows_fwd(views, b, (long long)nimg * H, H, W, g.pw, f.fft_tables, st);
+    if (e == cudaSuccess) e = launch_gen_cols(b, b, nimg, H, W, false, g.ph, f.fft_tables, nullptr, 1, st);
+    if (e != cudaSuccess) return FDL_ECUDA;
+    return run_solve(b, K, C, H, W, u, d, N, opts, layers, f, st);
+  }
   cudaError_t e = launch_twiddle_tables(f.fft_tables, H, W, st);
   if (e == cudaSuccess) e = launch_rfft_rows_df(views, f.spec_main, (long long)nimg * H, W, f.fft_tables, st);
   SpecView b = spec_split(f.spec_main, f.spec_nyq, H, W);
@@ -324,11 +411,10 @@ FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H,
   fdl_request* req = cv.take<fdl_request>(B);
   float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
   float2* nyq = cv.take<float2>((size_t)B * C * H);
+  float4* tables = cv.take<float4>(inv_table_elems(H, W));
   cudaError_t e = launch_pinhole_requests(req, layers, d, N, u0, B, out, (long long)C * H * W, st);
-  if (e == cudaSuccess) e = launch_render_spectra(req, B, nullptr, C, H, W, N, spec_split(main, nyq, H, W), st);
-  if (e == cudaSuccess) e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, nullptr, C, st);
-  if (e == cudaSuccess)
-    e = launch_irfft_rows(main, out, (long long)B * C * H, H, W, 1.f / ((float)H * (float)W), nullptr, nullptr, C, st);
+  if (e == cudaSuccess) e = launch_render_spectra(req, B, nullptr, C, H, W, N, render_spec_view(main, nyq, H, W), st);
+  if (e == cudaSuccess) e = render_inverse(main, nyq, tables, B, C, H, W, out, nullptr, nullptr, st);
   return cuda_status(e);
 }
 
@@ -346,10 +432,9 @@ FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, 
   Carver cv(workspace);
   float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
   float2* nyq = cv.take<float2>((size_t)B * C * H);
-  cudaError_t e = launch_render_spectra(req, B, count, C, H, W, Nmax, spec_split(main, nyq, H, W), st);
-  if (e == cudaSuccess) e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, count, C, st);
-  if (e == cudaSuccess)
-    e = launch_irfft_rows(main, nullptr, (long long)B * C * H, H, W, 1.f / ((float)H * (float)W), req, count, C, st);
+  float4* tables = cv.take<float4>(inv_table_elems(H, W));
+  cudaError_t e = launch_render_spectra(req, B, count, C, H, W, Nmax, render_spec_view(main, nyq, H, W), st);
+  if (e == cudaSuccess) e = render_inverse(main, nyq, tables, B, C, H, W, nullptr, req, count, st);
   return cuda_status(e);
 }
 

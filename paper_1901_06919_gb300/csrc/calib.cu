@@ -52,8 +52,10 @@ __global__ void __launch_bounds__(kCalibWarps * 32) k_calib(CalibParams cp) {
     if (qd < 0 || qd >= cp.H * (M + 1)) continue;  // out-of-range entries of a caller's list are skipped
     const int ky = qd / (M + 1), kx = qd - ky * (M + 1);
     hp_solve_bin<T>(p, ky, kx, G, Arow, Y);
-    const float wy = freq_y(ky, cp.H);
-    const float wx = (float)kx / (float)cp.W;
+    const Freq fq0 = bin_freq(ky, kx, cp.H, cp.W);
+    const auto fq = freq_prep(fq0, T{});
+    // w in double for the gradient factors of Eq. gradP
+    const double wx = (double)kx / (double)cp.W, wy = (double)fq0.kyp / (double)cp.H;
     // lambda x* Gamma*Gamma x (Gamma independent of d)
     if (lane < C) {
       const int c = lane;
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) k_calib(CalibParams cp) {
     }
     for (int j = 0; j < K; ++j) {
       const float2 uj = __ldg(reinterpret_cast<const float2*>(cp.u) + j);
-      const auto th = theta_r(uj.x, uj.y, wx, wy, T{});
+      const auto th = theta_r(uj.x, uj.y, fq, T{});
       for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(phase_r(th, __ldg(cp.d + r)), cp.exp_table);
       __syncwarp();
       if (lane < C) {
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(kCalibWarps * 32) k_calib(CalibParams cp) {
         loss_lane += rr * rr + ri * ri;
       }
       __syncwarp();
-      const double thd = (double)uj.x * (double)wx + (double)uj.y * (double)wy;
+      const double thd = (double)uj.x * wx + (double)uj.y * wy;
       double sj = 0.0;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -102,8 +104,8 @@ __global__ void __launch_bounds__(kCalibWarps * 32) k_calib(CalibParams cp) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
       if (lane == 0) {
-        acc[1 + 2 * j] += (double)wx * sj;
-        acc[1 + 2 * j + 1] += (double)wy * sj;
+        acc[1 + 2 * j] += wx * sj;
+        acc[1 + 2 * j + 1] += wy * sj;
       }
       __syncwarp();
     }

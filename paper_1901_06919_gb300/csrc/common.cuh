@@ -228,13 +228,46 @@ __device__ __forceinline__ float freq_y(int ky, int H) {
   return (ky < (H + 1) / 2 ? (float)ky : (float)(ky - H)) / (float)H;
 }
 
-// Phase of A_jk in cycles, reduced to [-1/2, 1/2]:  t = d (u_x w_x + u_y w_y).
-// w_x = kx/W and w_y are exact binary fractions; the products are kept exact
-// (TwoProd) so that the reduced phase is accurate to a few ulp of 1/2.
-__device__ __forceinline__ float phase_cycles(float ux, float uy, float wx, float wy, float d) {
+// Frequency of stored bin (ky, kx), w = (ky', kx) / (H, W) with ky' = ky or ky - H: the
+// correctly rounded quotient plus the float remainder of the division (wy + wy_lo,
+// wx + wx_lo equal w to ~2^-48 relative; the remainders are 0 when H and W are powers of
+// two, where the quotients are exact binary fractions).
+struct Freq {
+  float wy, wx, wy_lo, wx_lo;
+  int kyp, kx, H, W;
+};
+__device__ __forceinline__ Freq bin_freq(int ky, int kx, int H, int W) {
+  Freq f;
+  f.kyp = ky < (H + 1) / 2 ? ky : ky - H;
+  f.kx = kx;
+  f.H = H;
+  f.W = W;
+  f.wy = __fdiv_rn((float)f.kyp, (float)H);
+  f.wx = __fdiv_rn((float)kx, (float)W);
+  // k - w n is exact (the remainder of a correctly rounded quotient)
+  f.wy_lo = __fdiv_rn(fmaf(-f.wy, (float)H, (float)f.kyp), (float)H);
+  f.wx_lo = __fdiv_rn(fmaf(-f.wx, (float)W, (float)kx), (float)W);
+  return f;
+}
+
+// Phase in cycles reduced to [-1/2, 1/2]:  t = d (u_x w_x + u_y w_y) with w_x, w_y exact
+// binary fractions; the products are kept exact (TwoProd).
+__device__ __forceinline__ float phase_cycles_f(float ux, float uy, float wx, float wy, float d) {
   df px = two_prod(ux, wx);
   df py = two_prod(uy, wy);
   df th = df_add(px, py);
+  df t = df_mul_f(th, d);
+  const float n = rintf(t.hi);
+  return __fadd_rn(__fsub_rn(t.hi, n), t.lo);
+}
+
+// Phase of A_jk in cycles, reduced to [-1/2, 1/2]:  t = d (u . w), accurate to a few ulp
+// of 1/2 (the remainders of w enter the low word).
+__device__ __forceinline__ float phase_cycles(float ux, float uy, const Freq& f, float d) {
+  df px = two_prod(ux, f.wx);
+  df py = two_prod(uy, f.wy);
+  df th = df_add(px, py);
+  th = df_add_f(th, fmaf(ux, f.wx_lo, uy * f.wy_lo));
   df t = df_mul_f(th, d);
   const float n = rintf(t.hi);
   return __fadd_rn(__fsub_rn(t.hi, n), t.lo);

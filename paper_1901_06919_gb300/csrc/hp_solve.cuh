@@ -40,17 +40,28 @@ __device__ __forceinline__ float layer2_gtg(int i, int l, int N) {
 // large |d theta| is; rounding theta and d theta as double-floats instead
 // would leave 2^-47 |d theta|, which at |d theta| ~ 20 cycles (views at
 // |u| ~ 9) dominated the error of ill-conditioned frequencies.
-__device__ __forceinline__ R64 theta_r(float ux, float uy, float wx, float wy, R64) {
-  return {(double)ux * (double)wx + (double)uy * (double)wy};
+// The frequency as each arithmetic wants it, formed once per bin: FP64 divides the
+// integers; double-float keeps the float quotients and remainders.
+struct FreqD {
+  double wx, wy;
+};
+__device__ __forceinline__ FreqD freq_prep(const Freq& f, R64) {
+  return {(double)f.kx / (double)f.W, (double)f.kyp / (double)f.H};
+}
+__device__ __forceinline__ const Freq& freq_prep(const Freq& f, Rdf) { return f; }
+
+__device__ __forceinline__ R64 theta_r(float ux, float uy, const FreqD& f, R64) {
+  return {(double)ux * f.wx + (double)uy * f.wy};
 }
 __device__ __forceinline__ R64 phase_r(R64 th, float d) { return {th.v * (double)d}; }
 
 struct ThetaX {
   float p1, e1, p2, e2;
+  float g;  // u . (remainders of w): 0 for power-of-two sizes
 };
-__device__ __forceinline__ ThetaX theta_r(float ux, float uy, float wx, float wy, Rdf) {
-  const df a = two_prod(ux, wx), b = two_prod(uy, wy);
-  return {a.hi, a.lo, b.hi, b.lo};
+__device__ __forceinline__ ThetaX theta_r(float ux, float uy, const Freq& f, Rdf) {
+  const df a = two_prod(ux, f.wx), b = two_prod(uy, f.wy);
+  return {a.hi, a.lo, b.hi, b.lo, fmaf(ux, f.wx_lo, uy * f.wy_lo)};
 }
 __device__ __forceinline__ Rdf phase_r(const ThetaX& t, float d) {
   const df a = two_prod(d, t.p1), b = two_prod(d, t.p2);  // exact
@@ -59,12 +70,21 @@ __device__ __forceinline__ Rdf phase_r(const ThetaX& t, float d) {
   const df m1 = two_sum(a.lo, b.lo);
   const df m2 = two_sum(c.hi, e.hi);
   df m = two_sum(m1.hi, m2.hi);
-  m.lo = __fadd_rn(m.lo, __fadd_rn(__fadd_rn(m1.lo, m2.lo), __fadd_rn(c.lo, e.lo)));
+  // d g: rounding 2^-24 |d g| ~ 2^-48 |d theta| (only for sizes that are not powers of two)
+  const df m3 = two_sum(m.hi, d * t.g);
+  m = {m3.hi, __fadd_rn(__fadd_rn(m.lo, m3.lo), __fadd_rn(__fadd_rn(m1.lo, m2.lo), __fadd_rn(c.lo, e.lo)))};
   // |s| <= 1 and |m| ~ 2^-24 |d theta|: the sloppy double-word addition (error ~2^-46
   // (|s| + |m|)) keeps the absolute error of the phase at that level
   const df v = two_sum(s.hi, m.hi);
   return {fast_two_sum(v.hi, __fadd_rn(v.lo, __fadd_rn(s.lo, m.lo)))};
 }
+
+// w in the solve's arithmetic: FP64 from the integers, double-float from the quotient and
+// its remainder
+__device__ __forceinline__ R64 freq_x_r(const FreqD& f, R64) { return {f.wx}; }
+__device__ __forceinline__ R64 freq_y_r(const FreqD& f, R64) { return {f.wy}; }
+__device__ __forceinline__ Rdf freq_x_r(const Freq& f, Rdf) { return {{f.wx, f.wx_lo}}; }
+__device__ __forceinline__ Rdf freq_y_r(const Freq& f, Rdf) { return {{f.wy, f.wy_lo}}; }
 
 // exp(2 pi i t), FP64: CUDA's sincospi after reduction to [-1/2, 1/2].
 __device__ __forceinline__ cx<R64> cexp2pi(R64 t, const float4*) {
@@ -131,14 +151,14 @@ __device__ bool hp_solve_bin(const HpProblem& p, int ky, int kx, cx<T>* G, cx<T>
   const int N = p.N, C = p.C, M = p.W >> 1;
   const int ld = N + 1;
   const T zero = r_from(0.f, T{});
-  const float wy = freq_y(ky, p.H);
-  const float wx = (float)kx / (float)p.W;
+  const Freq fq0 = bin_freq(ky, kx, p.H, p.W);
+  const auto fq = freq_prep(fq0, T{});
   for (int e = lane; e < N * ld; e += 32) G[e] = {zero, zero};
   for (int e = lane; e < N * C; e += 32) Y[e] = {zero, zero};
   __syncwarp();
   for (int j = 0; j < p.K; ++j) {
     const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
-    const auto th = theta_r(uj.x, uj.y, wx, wy, T{});
+    const auto th = theta_r(uj.x, uj.y, fq, T{});
     for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(phase_r(th, __ldg(p.d + r)), p.exp_table);
     __syncwarp();
     float2 bj[4];
@@ -155,7 +175,7 @@ __device__ bool hp_solve_bin(const HpProblem& p, int ky, int kx, cx<T>* G, cx<T>
     __syncwarp();
   }
   {
-    const T wxr = r_from(wx, T{}), wyr = r_from(wy, T{});
+    const T wxr = freq_x_r(fq, T{}), wyr = freq_y_r(fq, T{});
     const T w2 = wxr * wxr + wyr * wyr;
     const T w4 = w2 * w2;
     const T lam = r_from_double(p.lam, T{});

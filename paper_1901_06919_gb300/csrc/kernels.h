@@ -82,6 +82,42 @@ bool solve_df_supported(int N);
 cudaError_t launch_mom_check(const SolveParams& p, cudaStream_t st);
 cudaError_t launch_solve_df(const SolveParams& p, bool all_bins, cudaStream_t st);
 
+// ---- DFTs of lengths that are not powers of two (fft_gen.cu) -----------------
+constexpr int kGenMaxRadix = 32;        // largest prime factor transformed directly
+constexpr int kGenMaxPasses = 16;
+constexpr int kGenMaxLength = 4096;
+constexpr int kGenMaxBluestein = 4096;  // largest power-of-two length of a Bluestein convolution
+struct GenPlan {
+  int L;                        // transform length
+  int np;                       // radix passes of L (0 with Bluestein)
+  int radix[kGenMaxPasses];
+  int M;                        // Bluestein convolution length (0: direct)
+  int mp;                       // radix passes of M
+  int mradix[kGenMaxPasses];
+  int tw, chirp, twm, bhat;     // float4 offsets of the tables in the table area
+  int elems;                    // float4 elements of tables this plan uses
+};
+struct GenPlanM {
+  int np;
+  int radix[kGenMaxPasses];
+};
+// lengths up to kGenMaxLength whose prime factors are <= kGenMaxRadix, or whose
+// Bluestein length fits kGenMaxBluestein (L <= 2048)
+bool gen_supported(int L);
+// plan of length L with its tables starting at float4 offset `base`
+bool gen_plan(int L, int base, GenPlan* p);
+cudaError_t launch_gen_tables(const GenPlan& p, float4* tables, cudaStream_t st);
+// real rows (nrows = images * H, length W) -> half spectra (kx <= W/2) in `out`
+cudaError_t launch_gen_rows_fwd(const float* x, SpecView out, long long nrows, int H, int W, const GenPlan& pw,
+                                const float4* tables, cudaStream_t st);
+// columns of nimg half spectra from s to so (may alias; forward or inverse; images >= count*C skipped)
+cudaError_t launch_gen_cols(SpecView s, SpecView so, int nimg, int H, int W, bool inverse, const GenPlan& ph,
+                            const float4* tables, const int* count, int C, cudaStream_t st);
+// Hermitian-completed inverse of the rows, real part x scale, to `out` or the requests' outputs
+cudaError_t launch_gen_rows_inv(SpecView in, float* out, long long nrows, int H, int W, float scale,
+                                const fdl_request* req, const int* count, int C, const GenPlan& pw,
+                                const float4* tables, cudaStream_t st);
+
 // ---- tier selection (select.cu) ---------------------------------------------
 // Appends to `list` the frequencies with the largest err so that the rest keep
 // u * sqrt(sum err^2) <= budget * sqrt(sum xn2); scratch of select_scratch_bytes().

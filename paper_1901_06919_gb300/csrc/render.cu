@@ -18,7 +18,7 @@ __device__ __forceinline__ float2 aperture_hat(int kind, float radius, const flo
     float2 acc = make_float2(0.f, 0.f);
     for (int m = 0; m < npts; ++m) {
       const float2 pm = __ldg(reinterpret_cast<const float2*>(pts) + m);
-      const float f = phase_cycles(pm.x, pm.y, nux, nuy, -1.f);
+      const float f = phase_cycles_f(pm.x, pm.y, nux, nuy, -1.f);
       float sn, cs;
       sincospif(2.f * f, &sn, &cs);
       acc.x += cs;
@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   const bool valid = q < Qs;
   int ky, kx;
   bin_coords(valid ? q : 0, H, M, ky, kx);
-  const float wy = freq_y(ky, H);
-  const float wx = (float)kx / (float)W;
+  const Freq fq = bin_freq(ky, kx, H, W);
+  const float wy = fq.wy, wx = fq.wx;
+  const float wylo = fq.wy_lo, wxlo = fq.wx_lo;
   const float wabs = sqrtf(wx * wx + wy * wy);
   const long long plane = (long long)H * (M + 1);
   const long long off = (long long)ky * (M + 1) + kx;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
     for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
     if (b < Bact) {
       const fdl_request r = req[b];
-      const df theta = df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy));
+      const df theta = df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, wxlo, r.u0y * wylo));
       render_terms(r, sl, G, C, theta, wy, wx, wabs, plane, off, valid, nullptr, nullptr, lane, acc);
     }
 #pragma unroll
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   }
   for (int b = warp; b < Bact; b += kRenderWarps) {
     const fdl_request r = req[b];
-    const df theta = df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy));
+    const df theta = df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, wxlo, r.u0y * wylo));
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);

@@ -43,15 +43,18 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
   if (threadIdx.x < 4) cnt_local[threadIdx.x] = 0;
 
   const int Qs = p.H * (M + 1);
-  const int ntiles = Qs / kTileBins;
+  const int ntiles = (Qs + kTileBins - 1) / kTileBins;  // the last tile may be partial
   const float dl = lane < N ? __ldg(p.d + lane) : 0.f;
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int q = tile * kTileBins + warp;
+    // warps past the last bin of a partial tile solve the last bin again (every warp
+    // takes part in the CTA's barriers) and write nothing
+    const int q = min(tile * kTileBins + warp, Qs - 1);
+    const bool qown = tile * kTileBins + warp < Qs;
     int ky, kx;
     bin_coords(q, p.H, M, ky, kx);
-    const float wy = freq_y(ky, p.H);
-    const float wx = (float)kx / (float)p.W;
+    const Freq fq = bin_freq(ky, kx, p.H, p.W);
+    const float wy = fq.wy, wx = fq.wx;
 
     float2 G[NMAX];
 #pragma unroll
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       for (int e = threadIdx.x; e < nv * C * kTileBins; e += blockDim.x) {
         const int img = e / kTileBins, bi = e - img * kTileBins;
         int qy, qx;
-        bin_coords(tile * kTileBins + bi, p.H, M, qy, qx);
+        bin_coords(min(tile * kTileBins + bi, Qs - 1), p.H, M, qy, qx);
         bstage[e] = *p.b.at((long long)j0 * C + img, qy, qx, M);
       }
       __syncthreads();
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
         const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
         float2 a = make_float2(0.f, 0.f);
         if (lane < N) {
-          const float f = phase_cycles(uj.x, uj.y, wx, wy, dl);
+          const float f = phase_cycles(uj.x, uj.y, fq, dl);
           sincospif(2.f * f, &a.y, &a.x);
         }
         if (lane < NMAX) myA[lane] = a;
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
     const long long off = (long long)ky * (M + 1) + kx;
     // without the estimate a factorisation that broke down leaves zeros
     const bool broke = !ok;
-    if (lane < N) {
+    if (lane < N && qown) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         if (c < C) p.x[((long long)lane * C + c) * plane + off] = broke ? make_float2(0.f, 0.f) : y[c];
@@ -247,12 +250,12 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
       const float kappa = lmax * vnorm;
       const bool trusted = ok && finite && isfinite(kappa) && kappa <= p.kappa_max && isfinite(n2);
-      if (lane == 0) {
+      if (lane == 0 && qown) {
         p.err[q] = trusted ? kappa * sqrtf(n2) : INFINITY;
         p.xn2[q] = isfinite(n2) ? n2 : 0.f;
       }
     }
-    if (lane == 0) {
+    if (lane == 0 && qown) {
       if (estimate || !broke) atomicAdd(&cnt_local[0], 1);
       if (!estimate && broke) atomicAdd(&cnt_local[2], 1);
       if (!finite) atomicAdd(&cnt_local[3], 1);
@@ -351,7 +354,7 @@ cudaError_t launch_f32_n(const SolveParams& p, bool estimate, cudaStream_t st) {
   cudaError_t e = set_smem((const void*)k_solve_f32<NMAX>, smem);
   if (e != cudaSuccess) return e;
   // one tile per CTA: short CTAs let higher-priority work interleave
-  const int ntiles = p.H * (p.W / 2 + 1) / kTileBins;
+  const int ntiles = (p.H * (p.W / 2 + 1) + kTileBins - 1) / kTileBins;
   k_solve_f32<NMAX><<<ntiles, kTileBins * 32, smem, st>>>(p, estimate ? 1 : 0);
   return cudaGetLastError();
 }

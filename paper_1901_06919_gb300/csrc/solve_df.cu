@@ -192,6 +192,11 @@ __device__ __forceinline__ void acc_df(df& acc, df v) {
 template <int NMAX, int S, bool MOM>
 __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df(SolveParams p, int all_bins) {
   constexpr int R = (NMAX + 31) / 32;  // rows per lane in the solves
+  if (p.mom != nullptr) {
+    // exactly one of the moment and the general kernel runs (k_mom_check decided)
+    const bool mom_on = *((volatile int*)(p.counters + 8)) == 1;
+    if (mom_on != MOM) return;
+  }
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int N = p.N, C = p.C, K = p.K, M = p.W >> 1;
@@ -219,11 +224,6 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
 #define SR(s) (rl[s] >> 8)
 #define SL(s) (rl[s] & 255)
 #define SLOT_USED(s) (lane + 32 * (s) < E)
-  if (p.mom != nullptr) {
-    // exactly one of the moment and the general kernel runs (k_mom_check decided)
-    const bool mom_on = *((volatile int*)(p.counters + 8)) == 1;
-    if (mom_on != MOM) return;
-  }
   for (int i = lane; i < 2 * NMAX + 1; i += 32) Arow[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
   float2 em[R];  // e_m of this lane's moments (moment form)
@@ -236,8 +236,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
     const int q = all_bins ? li : p.flagged[li];
     int ky, kx;
     bin_coords(q, p.H, M, ky, kx);
-    const float wy = freq_y(ky, p.H);
-    const float wx = (float)kx / (float)p.W;
+    const Freq fq = bin_freq(ky, kx, p.H, p.W);
 
     dfc G[S];
 #pragma unroll
@@ -270,7 +269,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
 
     for (int j = 0; j < K; ++j) {
       const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
-      const ThetaX th = theta_r(uj.x, uj.y, wx, wy, Rdf{});
+      const ThetaX th = theta_r(uj.x, uj.y, fq, Rdf{});
       float2 bj[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) bj[c] = c < C ? *p.b.at((long long)j * C + c, ky, kx, M) : make_float2(0.f, 0.f);
@@ -300,7 +299,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
       }
       if constexpr (MOM) {
         // w_jm = A_jm conj(A_j0) for this lane's m (A_j0 from lane 0) and the moments of w - 1
-        const df theta = df_add(two_sum(th.p1, th.p2), df_from(__fadd_rn(th.e1, th.e2)));
+        const df theta = df_add(two_sum(th.p1, th.p2), df_from(__fadd_rn(__fadd_rn(th.e1, th.e2), th.g)));
         const float th2 = theta.hi * theta.hi, th3 = th2 * theta.hi;
         acc_df(T1, theta);
         T2 += th2;
@@ -443,7 +442,8 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
 
     // lambda Gamma*Gamma
     {
-      const df w2 = df_add(two_prod(wx, wx), two_prod(wy, wy));
+      const df wxd = {fq.wx, fq.wx_lo}, wyd = {fq.wy, fq.wy_lo};
+      const df w2 = df_add(df_mul(wxd, wxd), df_mul(wyd, wyd));
       const df w4 = df_mul(w2, w2);
       const df lam = df_from_double(p.lam_d);
       const df lame = df_from_double(p.lam_eps_d);

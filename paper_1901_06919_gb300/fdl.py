@@ -48,6 +48,16 @@ def _opts(lam, eps, reg, precision, kappa_max, df_error_budget=0.0, f32_error_bu
                      float(f32_error_budget))
 
 
+def _width(Wh: int, W: int | None) -> int:
+    """Image width of a stored half of ``Wh`` columns: ``W`` if given (an odd width cannot be
+    told from ``Wh``), else the even width ``2 (Wh - 1)``."""
+    if W is None:
+        return 2 * (Wh - 1)
+    if W // 2 + 1 != Wh:
+        raise ValueError(f"width {W} does not match a stored half of {Wh} columns")
+    return int(W)
+
+
 # ---------------------------------------------------------------- DFTs
 def rfft2(images: torch.Tensor, stream=None) -> torch.Tensor:
     """Half spectra (complex64 ``[..., H, W//2+1]``) of float32 images ``[..., H, W]``."""
@@ -112,13 +122,14 @@ def fit(views: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, eps: 
 def fit_spectra(spectra: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, eps: float = 1e-4,
                 reg: str = "view2", precision: str = "mixed", kappa_max: float = 0.0,
                 out: torch.Tensor | None = None, ws: FitWorkspace | None = None, stream=None,
-                df_error_budget: float = 0.0, f32_error_budget: float = 0.0):
-    """Per-frequency solve from half spectra ``[K][C][H][W//2+1]``; returns ``(layers, workspace)``."""
+                df_error_budget: float = 0.0, f32_error_budget: float = 0.0, W: int | None = None):
+    """Per-frequency solve from half spectra ``[K][C][H][W//2+1]``; returns ``(layers, workspace)``.
+    ``W``: image width, needed when it is odd."""
     _need(spectra, torch.complex64, "spectra", 4)
     _need(u, torch.float32, "u", 2)
     _need(d, torch.float32, "d", 1)
     K, C, H, Wh = spectra.shape
-    W = 2 * (Wh - 1)
+    W = _width(Wh, W)
     N = d.numel()
     lib = _lib()
     if out is None:
@@ -134,13 +145,14 @@ def fit_spectra(spectra: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: fl
 
 # ---------------------------------------------------------------- render
 def render(layers: torch.Tensor, d: torch.Tensor, u0: torch.Tensor, out: torch.Tensor | None = None,
-           ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Sub-aperture views (Eq. FourierView) at ``u0 [B][2]``: float32 ``[B][C][H][W]``."""
+           ws: torch.Tensor | None = None, stream=None, W: int | None = None) -> torch.Tensor:
+    """Sub-aperture views (Eq. FourierView) at ``u0 [B][2]``: float32 ``[B][C][H][W]``
+    (``W``: image width, needed when it is odd)."""
     _need(layers, torch.complex64, "layers", 4)
     _need(d, torch.float32, "d", 1)
     _need(u0, torch.float32, "u0", 2)
     N, C, H, Wh = layers.shape
-    W = 2 * (Wh - 1)
+    W = _width(Wh, W)
     B = u0.shape[0]
     lib = _lib()
     if out is None:
@@ -164,6 +176,7 @@ class RenderSpec:
     radius: float = 0.0
     pts: torch.Tensor | None = None
     out: torch.Tensor | None = None
+    W: int | None = None  # image width, needed when it is odd
 
 
 def pack_requests(specs: list[RenderSpec], device) -> torch.Tensor:
@@ -172,7 +185,7 @@ def pack_requests(specs: list[RenderSpec], device) -> torch.Tensor:
     for i, sp in enumerate(specs):
         N, C, H, Wh = sp.layers.shape
         if sp.out is None:
-            sp.out = torch.empty((C, H, 2 * (Wh - 1)), dtype=torch.float32, device=device)
+            sp.out = torch.empty((C, H, _width(Wh, sp.W)), dtype=torch.float32, device=device)
         arr[i] = L.Request(sp.layers.data_ptr(), sp.d.data_ptr(), sp.out.data_ptr(),
                            sp.pts.data_ptr() if sp.pts is not None else None, N,
                            0 if sp.pts is None else sp.pts.shape[0], L.APERTURE[sp.aperture],
@@ -198,19 +211,19 @@ def refocus_specs(specs: list[RenderSpec], stream=None) -> list[torch.Tensor]:
     req = pack_requests(specs, dev)
     N, C, H, Wh = specs[0].layers.shape
     Nmax = max(s.layers.shape[0] for s in specs)
-    refocus(req, len(specs), C, H, 2 * (Wh - 1), Nmax, stream=stream)
+    refocus(req, len(specs), C, H, _width(Wh, specs[0].W), Nmax, stream=stream)
     return [s.out for s in specs]
 
 
 # ---------------------------------------------------------------- calibration
 def calib_grad(spectra: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, reg: str = "layer2",
-               bins: torch.Tensor | None = None, precision: str = "df", stream=None):
+               bins: torch.Tensor | None = None, precision: str = "df", stream=None, W: int | None = None):
     """Loss of Eq. CalibrationProb and its gradient w.r.t. u [K][2] and d [N] (Eqs. gradP, gradD)."""
     _need(spectra, torch.complex64, "spectra", 4)
     _need(u, torch.float32, "u", 2)
     _need(d, torch.float32, "d", 1)
     K, C, H, Wh = spectra.shape
-    W = 2 * (Wh - 1)
+    W = _width(Wh, W)
     N = d.numel()
     nb = 0
     if bins is not None:

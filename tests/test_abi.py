@@ -50,8 +50,16 @@ def test_status_strings(lib):
 
 def test_workspace_queries(lib):
     assert lib.fdl_fit_workspace_size(81, 3, 512, 512, 30) > 81 * 3 * 512 * 256 * 8
-    assert lib.fdl_fit_workspace_size(9, 1, 64, 48, 8) == 0  # W not a power of two
+    # the paper's sizes that are not powers of two: 625 x 434 (prime factors <= 31),
+    # 379 x 379 (prime: Bluestein), 1920 x 1080
+    assert lib.fdl_fit_workspace_size(81, 3, 434, 625, 30) >= 81 * 3 * 434 * 313 * 8
+    assert lib.fdl_fit_workspace_size(49, 3, 379, 379, 30) > 0
+    assert lib.fdl_rfft2_workspace_size(1, 1080, 1920) > 0
+    assert lib.fdl_render_workspace_size(4, 3, 434, 625) >= 4 * 3 * 434 * 313 * 8
+    # a prime above 2048 has no Bluestein length within 4096; sizes below 16 are refused
+    assert lib.fdl_fit_workspace_size(9, 1, 64, 2053, 8) == 0
     assert lib.fdl_rfft2_workspace_size(4, 8, 64) == 0  # H below 16
+    assert lib.fdl_irfft2_workspace_size(4, 64, 15) == 0  # W below 16
     assert lib.fdl_render_workspace_size(113, 3, 512, 512) >= 113 * 3 * 512 * 257 * 8
     assert lib.fdl_refocus_workspace_size(0, 3, 512, 512) == 0
     assert lib.fdl_calib_grad_workspace_size(25, 1, 256, 256, 12, 4096) > 0
@@ -72,7 +80,7 @@ def test_fit_rejects_bad_arguments_before_any_launch(lib):
     assert call(K=0) == L.FDL_EINVAL
     assert call(C=5) == L.FDL_EINVAL
     assert call(N=65) == L.FDL_EINVAL
-    assert call(H=48) == L.FDL_EINVAL
+    assert call(H=2053) == L.FDL_EINVAL  # prime above 2048: no supported DFT length
     assert call(W=8192) == L.FDL_EINVAL
     assert call(opts=None) == L.FDL_EINVAL
     assert call(opts=_opts(lam=-1.0)) == L.FDL_EINVAL
