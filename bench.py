@@ -484,6 +484,54 @@ class Fp64Render:
 
 
 # ------------------------------------------------------------------ precision form
+# The paper's own light-field shapes (Sec. VII timing table; Matlab on a GTX 1080, context only):
+# name, (H, W), view grid half-width, layer construction s, render ms
+PAPER_SHAPES = [("Fruits 625x434x9x9", (434, 625), 4, 0.9, 12.0),
+                ("Totoro WaterFall 379x379x7x7", (379, 379), 3, 0.4, 7.0),
+                ("Chess Pieces 1920x1080x5x5", (1080, 1920), 2, 4.3, 53.0)]
+
+
+def shapes_leg(device, reps=3):
+    """Fit (DFT + tiers) and single-view render at the paper's sizes that are not powers of
+    two, RGB, N = 30 layers on linspace(-3, 3), lambda = 1e-2, synthetic occluding planes."""
+    import torch
+
+    import paper_1901_06919_gb300 as F
+    from scenes import occluding_planes, view_grid
+
+    out = {}
+    for name, (H, W), g, paper_fit_s, paper_render_ms in PAPER_SHAPES:
+        u = view_grid(g)
+        d = np.linspace(-3, 3, N).astype(np.float32)
+        views, _ = occluding_planes(11, H, W, C, u)
+        V, U, D = (torch.from_numpy(a).to(device) for a in (views, u, d))
+        x, ws = F.fit(V, U, D, LAM, EPS)
+        u0 = torch.tensor([[0.3, -0.2]], dtype=torch.float32, device=device)
+        img = F.render(x, D, u0, W=W)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            F.fit(V, U, D, LAM, EPS, out=x, ws=ws)
+        b.record()
+        torch.cuda.synchronize()
+        fit_ms = a.elapsed_time(b) / reps
+        a.record()
+        for _ in range(10):
+            F.render(x, D, u0, out=img, W=W)
+        b.record()
+        torch.cuda.synchronize()
+        render_ms = a.elapsed_time(b) / 10
+        q = H * (W // 2 + 1)
+        out[name] = {"fit_ms": fit_ms, "fit_mfreq_s": q / fit_ms / 1e3, "render_ms": render_ms,
+                     "tiers": ws.tier_counts(), "paper_gtx1080_fit_ms": paper_fit_s * 1e3,
+                     "paper_gtx1080_render_ms": paper_render_ms}
+        del V, x, ws, img
+        torch.cuda.empty_cache()
+    return out
+
+
 def precision_leg(device, lams=(1e-3, 1e-2, 1e-1), nb=24):
     """7x7 views, 1024x1024 RGB, N=40 on linspace(-4, 4): fit time and layer error per lambda
     against the FP64 oracle on a sample of frequencies (low ones, where conditioning is worst,
@@ -662,6 +710,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the torch FP64 comparator leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-precision", action="store_true", help="skip the 1024x1024 precision leg")
+    ap.add_argument("--no-shapes", action="store_true", help="skip the leg at the paper's non-power-of-two sizes")
     ap.add_argument("--no-calib", action="store_true", help="skip the calibration leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -740,6 +789,8 @@ def main():
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_precision:
         line["precision"] = precision_leg(device)
+    if rank == 0 and not args.no_shapes:
+        line["paper_shapes"] = shapes_leg(device)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_calib:
         line["calibration"] = calib_leg(device)

@@ -22,13 +22,16 @@
  *   Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
  *     only enqueue work; they do not synchronise, except where stated.
  *   Complex numbers: interleaved float pairs (re, im), i.e. complex64.
- *   Images: float32 [C][H][W] row-major (y = row); H and W powers of two,
- *     16 <= H, W <= 4096.
+ *   Images: float32 [C][H][W] row-major (y = row); 16 <= H, W <= 4096, each
+ *     a power of two, or a length whose prime factors are all <= 31 (625,
+ *     434 = 2 x 7 x 31, 1080, 1920, ...), or any length <= 2048 (379, a
+ *     prime; transformed through Bluestein's convolution).  Other sizes are
+ *     rejected with FDL_EINVAL.
  *   Spectra: the non-negative-kx half of the 2D DFT, complex64
- *     [..][H][W/2+1] (the layout of torch.fft.rfft2).  Frequencies are in
- *     cycles per pixel: w_y = ky/H for ky < H/2, (ky-H)/H otherwise;
- *     w_x = kx/W for kx = 0..W/2.  The forward DFT is unnormalised with
- *     sign -: b(w) = sum_x B(x) exp(-2 pi i w.x).
+ *     [..][H][W/2+1] (the layout of torch.fft.rfft2; W/2 rounds down).
+ *     Frequencies are in cycles per pixel: w_y = ky/H for ky < (H+1)/2,
+ *     (ky-H)/H otherwise; w_x = kx/W for kx = 0..W/2.  The forward DFT is
+ *     unnormalised with sign -: b(w) = sum_x B(x) exp(-2 pi i w.x).
  *   Views: u is float32 [K][2] = (u_x, u_y) per view in view-grid units;
  *     a layer of disparity d is seen from u as layer(x + u d) (Appendix A,
  *     Eq. Prior2).  Disparities d are float32 [N], pixels per unit of u.
