@@ -34,7 +34,7 @@ import numpy as np
 from scipy.special import j1 as _bessel_j1
 
 REG_VIEW2, REG_LAYER2, REG_L2 = 0, 1, 2
-AP_PINHOLE, AP_DISC, AP_SQUARE, AP_POINTS = 0, 1, 2, 3
+AP_PINHOLE, AP_DISC, AP_SQUARE, AP_POINTS, AP_TABLE = 0, 1, 2, 3, 4
 
 
 # ----------------------------------------------------------------------------
@@ -268,16 +268,66 @@ def fit(views, u, d, lam: float, eps: float = 1e-4, reg: int = REG_VIEW2) -> np.
 # Rendering (Sec. VI-A, Eq. BsFourier)
 # ----------------------------------------------------------------------------
 
+def aperture_table(raster, Z: int) -> np.ndarray:
+    """Transform of a drawn aperture (Sec. VI-A: rasterise, zero-pad, DFT), half spectrum
+    ``[Z][Z//2+1]`` normalised to ``psi_hat(0) = 1``.
+
+    ``raster`` is ``[P][P]`` with P odd; pixel ``(iy, ix)`` sits at ``u = ((ix - c) h, (iy - c) h)``,
+    ``c = (P - 1) / 2``.  It is placed in a ``Z x Z`` array with its centre pixel at index 0
+    (wrap-around), so that table entry ``(gy, gx)`` is ``psi_hat`` at ``nu = (gy, gx) / (Z h)``.
+    """
+    R = np.asarray(raster, np.float64)
+    P = R.shape[0]
+    if R.shape != (P, P) or P % 2 == 0 or P > Z:
+        raise ValueError("the raster must be square with an odd side no larger than Z")
+    c = (P - 1) // 2
+    pad = np.zeros((Z, Z))
+    for iy in range(P):
+        for ix in range(P):
+            pad[(iy - c) % Z, (ix - c) % Z] += R[iy, ix]
+    return half_spectrum(pad) / R.sum()
+
+
+def aperture_lookup(T, h: float, nu_y, nu_x) -> np.ndarray:
+    """``psi_hat(nu)`` from a table of :func:`aperture_table` by bilinear interpolation
+    (Sec. VI-A: linear interpolation) on the grid ``nu = g / (Z h)``, periodic in ``g`` with
+    period Z, the columns not stored taken from ``psi_hat(-nu) = conj psi_hat(nu)``."""
+    T = np.asarray(T, np.complex128)
+    Z = T.shape[0]
+    gy = np.asarray(nu_y, np.float64) * Z * h
+    gx = np.asarray(nu_x, np.float64) * Z * h
+    y0 = np.floor(gy)
+    x0 = np.floor(gx)
+    fy = gy - y0
+    fx = gx - x0
+    y0 = y0.astype(np.int64)
+    x0 = x0.astype(np.int64)
+
+    def fetch(iy, ix):
+        iy = iy % Z
+        ix = ix % Z
+        stored = ix <= Z // 2
+        direct = T[iy, np.where(stored, ix, 0)]
+        mirror = np.conj(T[(-iy) % Z, np.where(stored, 0, Z - ix)])
+        return np.where(stored, direct, mirror)
+
+    return ((1 - fy) * (1 - fx) * fetch(y0, x0) + (1 - fy) * fx * fetch(y0, x0 + 1)
+            + fy * (1 - fx) * fetch(y0 + 1, x0) + fy * fx * fetch(y0 + 1, x0 + 1))
+
+
 def aperture_ft(kind: int, radius: float, nu_y, nu_x, points=None) -> np.ndarray:
     """``psi_hat(nu) = int psi(u) exp(-2 pi i u . nu) du`` with ``int psi = 1``.
 
     DISC of radius r: ``2 J1(2 pi r |nu|) / (2 pi r |nu|)``; SQUARE of half
     side r: ``sinc(2 r nu_x) sinc(2 r nu_y)`` (normalised sinc, as in
     Eq. GTG); POINTS: ``(1/M) sum_m exp(-2 pi i u_m . nu)`` for offsets
-    ``u_m`` given as they are; PINHOLE (or r = 0): 1 (Sec. III, psi = delta).
+    ``u_m`` given as they are; TABLE: :func:`aperture_lookup` of the table passed as
+    ``points`` with raster pitch ``h = radius``; PINHOLE (or r = 0): 1 (Sec. III, psi = delta).
     """
     nu_y = np.asarray(nu_y, np.float64)
     nu_x = np.asarray(nu_x, np.float64)
+    if kind == AP_TABLE:
+        return aperture_lookup(points, radius, nu_y, nu_x)
     if kind == AP_POINTS:
         pts = np.asarray(points, np.float64)
         ph = pts[:, 0].reshape((-1,) + (1,) * nu_x.ndim) * nu_x + \

@@ -138,3 +138,54 @@ def test_view_regulariser_is_mean_squared_angular_laplacian():
     x = X[:, 0, ky, kx]
     ref = np.real(np.conj(x) @ R @ x)
     assert abs(mean - ref) < 0.05 * ref
+
+
+# ---- drawn apertures (Sec. VI-A: rasterise, zero-pad, DFT, linear interpolation)
+
+def test_aperture_table_of_one_pixel_is_a_pinhole():
+    T = O.aperture_table(np.ones((1, 1)), 32)
+    assert np.allclose(T, 1.0, atol=1e-14)
+    rng = np.random.default_rng(0)
+    nu = rng.uniform(-3, 3, (2, 50))
+    assert np.allclose(O.aperture_lookup(T, 0.25, nu[0], nu[1]), 1.0, atol=1e-14)
+
+
+def test_aperture_table_nodes_are_the_point_set_transform():
+    """At table nodes the drawn aperture is exactly the discrete aperture of its pixels
+    (weights as point multiplicities), including an asymmetric raster."""
+    rng = np.random.default_rng(1)
+    R = rng.integers(0, 3, (5, 5)).astype(float)
+    R[2, 2] = 1.0
+    h, Z = 0.3, 64
+    T = O.aperture_table(R, Z)
+    pts = [((ix - 2) * h, (iy - 2) * h) for iy in range(5) for ix in range(5) for _ in range(int(R[iy, ix]))]
+    g = rng.integers(-40, 40, (2, 30))
+    nu_y, nu_x = g[0] / (Z * h), g[1] / (Z * h)
+    ref = O.aperture_ft(O.AP_POINTS, 0.0, nu_y, nu_x, np.array(pts))
+    got = O.aperture_lookup(T, h, nu_y, nu_x)
+    assert np.allclose(got, ref, atol=1e-12)
+    assert np.allclose(O.aperture_lookup(T, h, -nu_y, -nu_x), np.conj(got), atol=1e-12)
+
+
+def test_aperture_table_interpolation_error_shrinks_with_padding():
+    """Between nodes the bilinear value approaches the transform with the error of linear
+    interpolation, O((grid spacing)^2)."""
+    R = np.ones((3, 3))
+    h = 0.5
+    pts = np.array([((ix - 1) * h, (iy - 1) * h) for iy in range(3) for ix in range(3)])
+    rng = np.random.default_rng(2)
+    nu = rng.uniform(-1.5, 1.5, (2, 200))
+    ref = O.aperture_ft(O.AP_POINTS, 0.0, nu[0], nu[1], pts)
+    errs = [np.max(np.abs(O.aperture_lookup(O.aperture_table(R, Z), h, nu[0], nu[1]) - ref)) for Z in (32, 64, 128)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 2e-3 and errs[1] / errs[2] > 3.0
+
+
+def test_render_with_a_one_pixel_table_is_the_pinhole_render():
+    rng = np.random.default_rng(3)
+    X = (rng.standard_normal((3, 1, 16, 9)) + 1j * rng.standard_normal((3, 1, 16, 9)))
+    d = np.array([-1.0, 0.0, 1.5])
+    T = O.aperture_table(np.ones((1, 1)), 16)
+    a = O.render(X, d, (0.3, -0.2), 0.7, O.AP_TABLE, 0.4, T)
+    b = O.render(X, d, (0.3, -0.2), 0.7, O.AP_PINHOLE, 0.0)
+    assert np.allclose(a, b, atol=1e-13)
