@@ -81,6 +81,8 @@ extern "C" {
 #define FDL_AP_DISC 1    /* disc of radius r: 2 J1(2 pi r|v|) / (2 pi r|v|)    */
 #define FDL_AP_SQUARE 2  /* square of half side r: sinc(2 r v_x) sinc(2 r v_y) */
 #define FDL_AP_POINTS 3  /* (1/M) sum_m delta(u - u_m): discrete aperture     */
+#define FDL_AP_TABLE 4   /* drawn aperture: psi_hat interpolated bilinearly in a
+                            table of fdl_aperture_table (Sec. VI-A)            */
 
 typedef struct fdl_fit_opts {
   double lambda;    /* Tikhonov weight lambda of Eq. LayerConstructProb, >= 0      */
@@ -113,13 +115,16 @@ typedef struct fdl_request {
   const float* layers; /* device complex64 [N][C][H][W/2+1]                     */
   const float* d;      /* device float32 [N]                                    */
   float* out;          /* device float32 [C][H][W]                              */
-  const float* pts;    /* FDL_AP_POINTS: device float32 [npts][2] offsets u_m   */
+  const float* pts;    /* FDL_AP_POINTS: device float32 [npts][2] offsets u_m;
+                          FDL_AP_TABLE: device complex64 [npts][npts/2+1], a
+                          table of fdl_aperture_table with Z = npts            */
   int N, npts;
   int aperture;        /* FDL_AP_*                                              */
   float u0x, u0y;      /* viewpoint on the camera plane                         */
   float s;             /* refocus parameter (disparity in focus), Sec. III      */
   float radius;        /* disc radius / square half side, in units of u (the
-                          aperture-size factor f of Sec. VI-A)                  */
+                          aperture-size factor f of Sec. VI-A); FDL_AP_TABLE:
+                          the raster pitch h, in units of u                     */
   int pad_;            /* keeps the struct a multiple of 8 bytes; set to 0      */
 } fdl_request;
 
@@ -201,6 +206,19 @@ FDL_API size_t fdl_refocus_workspace_size(int B, int C, int H, int W);
 FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, int H,
                         int W, int Nmax, void* workspace, size_t workspace_bytes,
                         void* stream);
+
+/* Table of a drawn aperture (Sec. VI-A: the aperture is drawn, zero-padded
+ * and transformed, and psi_hat is linearly interpolated).  raster: DEVICE
+ * float32 [P][P], P odd, 1 <= P <= Z; pixel (iy, ix) sits at u = ((ix - c) h,
+ * (iy - c) h), c = (P-1)/2, for the pitch h that the requests give in
+ * `radius`.  table: DEVICE complex64 [Z][Z/2+1] = psi_hat at nu = (gy, gx) /
+ * (Z h) for the stored half, normalised so that psi_hat(0) = 1 (the raster's
+ * sum must be positive).  Z is an image size the DFTs accept.  A request with
+ * FDL_AP_TABLE interpolates it bilinearly, periodic in Z, with psi_hat(-nu) =
+ * conj psi_hat(nu) for the columns not stored. */
+FDL_API size_t fdl_aperture_table_workspace_size(int P, int Z);
+FDL_API int fdl_aperture_table(const float* raster, int P, int Z, float* table, void* workspace,
+                               size_t workspace_bytes, void* stream);
 
 /* ---- calibration (Sec. V-B) ------------------------------------------- */
 

@@ -8,6 +8,7 @@ from ._lib import FdlError, load  # noqa: F401
 from .fdl import (  # noqa: F401
     FitWorkspace,
     RenderSpec,
+    aperture_table,
     calib_grad,
     fit,
     fit_spectra,

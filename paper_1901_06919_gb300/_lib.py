@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_PKG, "libfdl.so")
 FDL_OK, FDL_EINVAL, FDL_ENOMEM, FDL_ECUDA, FDL_ETIMEOUT, FDL_ENOTSUP = range(6)
 REG = {"view2": 0, "layer2": 1, "l2": 2}
 PREC = {"mixed": 0, "df": 1, "f64": 2, "f32": 3}
-APERTURE = {"pinhole": 0, "disc": 1, "square": 2, "points": 3}
+APERTURE = {"pinhole": 0, "disc": 1, "square": 2, "points": 3, "table": 4}
 
 
 class FitOpts(ct.Structure):
@@ -63,6 +63,9 @@ _SIGS = [
     ("fdl_render", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
                               ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p]),
     ("fdl_refocus_workspace_size", ct.c_size_t, [ct.c_int] * 4),
+    ("fdl_aperture_table_workspace_size", ct.c_size_t, [ct.c_int] * 2),
+    ("fdl_aperture_table", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_size_t,
+                                      ct.c_void_p]),
     ("fdl_refocus", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
                                ct.c_void_p, ct.c_size_t, ct.c_void_p]),
     ("fdl_calib_grad_workspace_size", ct.c_size_t, [ct.c_int] * 6),

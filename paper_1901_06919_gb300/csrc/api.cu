@@ -418,6 +418,28 @@ FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H,
   return cuda_status(e);
 }
 
+// ------------------------------------------------------------------ drawn aperture
+FDL_API size_t fdl_aperture_table_workspace_size(int P, int Z) {
+  if (P < 1 || (P & 1) == 0 || P > Z || !shape_ok(Z, Z)) return 0;
+  return align_up((size_t)Z * Z * sizeof(float)) + align_up(sizeof(double)) + fdl_rfft2_workspace_size(1, Z, Z);
+}
+
+FDL_API int fdl_aperture_table(const float* raster, int P, int Z, float* table, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+  if (P < 1 || (P & 1) == 0 || P > Z || !shape_ok(Z, Z) || !raster || !table || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_aperture_table_workspace_size(P, Z)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(workspace);
+  float* pad = cv.take<float>((size_t)Z * Z);
+  double* sum = cv.take<double>(1);
+  void* ws2 = static_cast<char*>(workspace) + cv.off;
+  cudaError_t e = launch_aperture_table_prep(raster, P, Z, pad, sum, st);
+  if (e != cudaSuccess) return FDL_ECUDA;
+  const int s = fdl_rfft2(pad, 1, Z, Z, table, ws2, fdl_rfft2_workspace_size(1, Z, Z), stream);
+  if (s != FDL_OK) return s;
+  return cuda_status(launch_aperture_table_scale(reinterpret_cast<float2*>(table), Z, sum, st));
+}
+
 FDL_API size_t fdl_refocus_workspace_size(int B, int C, int H, int W) {
   if (B < 1 || C < 1 || C > 4 || !shape_ok(H, W)) return 0;
   return render_ws_bytes(B, C, H, W, false);

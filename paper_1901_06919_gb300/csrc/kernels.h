@@ -130,6 +130,9 @@ cudaError_t launch_select_budget(const float* err, const float* xn2, int n, doub
 // requests read one FDL.
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
                                   SpecView out, cudaStream_t st);
+// drawn aperture: centred zero-padded raster and its sum (double), then the table scaling
+cudaError_t launch_aperture_table_prep(const float* R, int P, int Z, float* pad, double* sum, cudaStream_t st);
+cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cudaStream_t st);
 cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N,
                                     const float* u0, int B, float* out, long long img_elems, cudaStream_t st);
 

@@ -41,6 +41,33 @@ __device__ __forceinline__ float2 aperture_hat(int kind, float radius, const flo
   return make_float2(fx * fy, 0.f);
 }
 
+// psi_hat(nu) of a drawn aperture: bilinear interpolation of the table T (half spectrum
+// [Z][Z/2+1] of fdl_aperture_table) at grid coordinates g = nu Z h, periodic in Z, with
+// T(-g) = conj T(g) for the columns not stored (Sec. VI-A).
+__device__ __forceinline__ float2 table_fetch(const float2* __restrict__ T, int Z, int iy, int ix) {
+  iy = iy >= Z ? iy - Z : iy;  // iy, ix in [0, 2Z)
+  ix = ix >= Z ? ix - Z : ix;
+  const int Zh = Z / 2 + 1;
+  if (ix <= Z / 2) return __ldg(T + (long long)iy * Zh + ix);
+  const float2 v = __ldg(T + (long long)(iy ? Z - iy : 0) * Zh + (Z - ix));
+  return make_float2(v.x, -v.y);
+}
+__device__ __forceinline__ float2 aperture_table_hat(const float2* __restrict__ T, int Z, float h, float nuy,
+                                                     float nux) {
+  if (Z < 1) return make_float2(1.f, 0.f);
+  float gy = nuy * (float)Z * h, gx = nux * (float)Z * h;
+  if (!(fabsf(gy) < 1e30f) || !(fabsf(gx) < 1e30f)) return make_float2(0.f, 0.f);
+  gy -= (float)Z * floorf(gy / (float)Z);  // [0, Z]
+  gx -= (float)Z * floorf(gx / (float)Z);
+  const float y0f = fminf(floorf(gy), (float)(Z - 1)), x0f = fminf(floorf(gx), (float)(Z - 1));
+  const float fy = gy - y0f, fx = gx - x0f;
+  const int y0 = max((int)y0f, 0), x0 = max((int)x0f, 0);
+  const float2 a = table_fetch(T, Z, y0, x0), b = table_fetch(T, Z, y0, x0 + 1);
+  const float2 c = table_fetch(T, Z, y0 + 1, x0), e = table_fetch(T, Z, y0 + 1, x0 + 1);
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  return make_float2(w00 * a.x + w01 * b.x + w10 * c.x + w11 * e.x, w00 * a.y + w01 * b.y + w10 * c.y + w11 * e.y);
+}
+
 // Phase of exp(+2 pi i d (u0 . w)) in cycles, reduced to [-1/2, 1/2], from
 // theta = u0 . w kept as a double-float (computed once per request and bin).
 __device__ __forceinline__ float phase_from_theta(df theta, float d) {
@@ -68,6 +95,8 @@ __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int k
     if (r.aperture == FDL_AP_DISC && r.radius != 0.f) {
       const float z = zscale * fabsf(sd);
       coef = cscale(sh, z < 1e-3f ? 1.f - 0.125f * z * z : 2.f * j1f(z) / z);
+    } else if (r.aperture == FDL_AP_TABLE) {
+      coef = cmul(sh, aperture_table_hat(reinterpret_cast<const float2*>(r.pts), r.npts, r.radius, sd * wy, sd * wx));
     } else if (r.aperture != FDL_AP_PINHOLE && r.aperture != FDL_AP_DISC) {
       coef = cmul(sh, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
     }
@@ -194,7 +223,55 @@ __global__ void k_pinhole_requests(fdl_request* req, const float* layers, const 
   req[b] = r;
 }
 
+// centred zero-padded raster: pad[iy'][ix'] = R[(iy' + c) mod Z][(ix' + c) mod Z] when that
+// pixel exists (P <= Z, so each padded entry has at most one source)
+__global__ void k_place_raster(const float* __restrict__ R, int P, int Z, float* __restrict__ pad) {
+  const long long n = (long long)Z * Z;
+  const int c = (P - 1) / 2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int iyp = (int)(e / Z), ixp = (int)(e - (long long)iyp * Z);
+    int iy = iyp + c, ix = ixp + c;
+    iy = iy >= Z ? iy - Z : iy;
+    ix = ix >= Z ? ix - Z : ix;
+    pad[e] = (iy < P && ix < P) ? R[iy * P + ix] : 0.f;
+  }
+}
+
+// sum of the raster in double, one CTA, fixed order: deterministic
+__global__ void k_raster_sum(const float* __restrict__ R, int n, double* __restrict__ out) {
+  __shared__ double part[256];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) s += (double)R[e];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = part[0];
+}
+
+__global__ void k_scale_table(float2* __restrict__ T, long long n, const double* __restrict__ sum) {
+  const double s = sum[0];
+  const float inv = s > 0.0 ? (float)(1.0 / s) : 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    T[e] = make_float2(T[e].x * inv, T[e].y * inv);
+}
+
 }  // namespace
+
+cudaError_t launch_aperture_table_prep(const float* R, int P, int Z, float* pad, double* sum, cudaStream_t st) {
+  const long long n = (long long)Z * Z;
+  k_place_raster<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(R, P, Z, pad);
+  k_raster_sum<<<1, 256, 0, st>>>(R, P * P, sum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cudaStream_t st) {
+  const long long n = (long long)Z * (Z / 2 + 1);
+  k_scale_table<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(T, n, sum);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
                                   SpecView out, cudaStream_t st) {

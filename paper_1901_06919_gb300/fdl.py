@@ -205,6 +205,20 @@ def refocus(req_dev: torch.Tensor, B: int, C: int, H: int, W: int, Nmax: int, co
             "fdl_refocus")
 
 
+def aperture_table(raster: torch.Tensor, Z: int, stream=None) -> torch.Tensor:
+    """Table of a drawn aperture (Sec. VI-A): complex64 ``[Z][Z//2+1]`` from an odd-sided float32
+    raster ``[P][P]`` centred on its middle pixel.  Render it with ``RenderSpec(...,
+    aperture="table", radius=h, pts=table)``, h being the raster pitch in units of u."""
+    _need(raster, torch.float32, "raster", 2)
+    P = raster.shape[0]
+    lib = _lib()
+    out = torch.empty((Z, Z // 2 + 1), dtype=torch.complex64, device=raster.device)
+    ws = workspace(lib.fdl_aperture_table_workspace_size(P, Z), raster.device)
+    L.check(lib.fdl_aperture_table(_p(raster), P, Z, _p(out), _p(ws), ws.numel(), _stream(stream)),
+            "fdl_aperture_table")
+    return out
+
+
 def refocus_specs(specs: list[RenderSpec], stream=None) -> list[torch.Tensor]:
     """Convenience: pack, render and return the output images of ``specs`` (same H, W, C)."""
     dev = specs[0].layers.device
