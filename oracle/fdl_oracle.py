@@ -427,3 +427,93 @@ def calib_loss_grad(b, wy, wx, u, d, lam: float, reg: int = REG_LAYER2):
 def calib_loss(b, wy, wx, u, d, lam: float, reg: int = REG_LAYER2) -> float:
     """Eq. CalibrationProb at its minimum over x, for fixed ``u, d``."""
     return calib_loss_grad(b, wy, wx, u, d, lam, reg)[0]
+
+
+# ----------------------------------------------------------------------------
+# The general system of Eq. AMatGeneral: free shifts (the relaxed model of the
+# denoising section, P without the rank-1 constraint P = u d^T) and per-view
+# apertures and focus (focal stacks and hybrid inputs, Sec. V)
+# ----------------------------------------------------------------------------
+
+def shifts_of(u, d) -> np.ndarray:
+    """``P[j, k] = u_j d_k`` as ``[K][N][2]`` (x, y): the rank-1 shifts of Sec. V-B."""
+    u = np.asarray(u, np.float64)
+    d = np.asarray(d, np.float64)
+    return u[:, None, :] * d[None, :, None]
+
+
+def system_matrix_general(wy, wx, P, d=None, views=None) -> np.ndarray:
+    """``A[q, j, k] = exp(+2 pi i P_jk . w_q) psi_hat_j((s_j - d_k) w_q)`` (Eq. AMatGeneral with
+    the shift ``u_j d_k`` replaced by ``P_jk``).  ``views[j] = (kind, radius, s, points)`` is the
+    aperture and focus of image j (None: every image a sub-aperture view, psi = delta); the
+    aperture argument needs ``d``."""
+    P = np.asarray(P, np.float64)
+    wy = np.atleast_1d(np.asarray(wy, np.float64))
+    wx = np.atleast_1d(np.asarray(wx, np.float64))
+    phase = wx[:, None, None] * P[None, :, :, 0] + wy[:, None, None] * P[None, :, :, 1]
+    A = np.exp(2j * np.pi * phase)
+    if views is not None:
+        d = np.asarray(d, np.float64)
+        for j, (kind, radius, s, pts) in enumerate(views):
+            nu_y = (s - d)[None, :] * wy[:, None]
+            nu_x = (s - d)[None, :] * wx[:, None]
+            A[:, j, :] = A[:, j, :] * aperture_ft(kind, radius, nu_y, nu_x, pts)
+    return A
+
+
+def solve_system(b, A, lam: float, R) -> np.ndarray:
+    """Closed form of Eq. LayerConstructionClosedForm for given ``A [q, K, N]``, ``R [q, N, N]``."""
+    AH = np.conj(np.swapaxes(A, -1, -2))
+    return gauss_solve(AH @ A + lam * R, AH @ np.asarray(b, np.complex128))
+
+
+def fit_spectra_general(b_half, P, lam: float, eps: float = 1e-4, reg: int = REG_VIEW2, d=None, views=None,
+                        W=None, chunk: int = 2048) -> np.ndarray:
+    """Layer spectra ``[N][C][H][W/2+1]`` for the general system (the view regulariser needs d)."""
+    K, C, H, Wh = b_half.shape
+    W = full_width(Wh, W)
+    N = np.asarray(P).shape[1]
+    wy, wx = half_grid(H, W)
+    bq = np.moveaxis(b_half.reshape(K, C, H * Wh), -1, 0)
+    dd = np.zeros(N) if d is None else np.asarray(d, np.float64)
+    if reg == REG_VIEW2 and d is None:
+        raise ValueError("the view regulariser needs the layer disparities")
+    xq = np.empty((H * Wh, N, C), np.complex128)
+    for s0 in range(0, H * Wh, chunk):
+        sl = slice(s0, s0 + chunk)
+        A = system_matrix_general(wy[sl], wx[sl], P, dd, views)
+        xq[sl] = solve_system(bq[sl], A, lam, regulariser(reg, dd, wy[sl], wx[sl], eps))
+    return np.moveaxis(xq, 0, -1).reshape(N, C, H, Wh)
+
+
+def render_shifts(layers, Pb, W=None) -> np.ndarray:
+    """Image ``sum_k layer_k`` shifted by ``Pb[k]`` (``[N][2]``), i.e. the view rendered with the
+    relaxed model's shifts (Eq. FourierView with ``u0 d_k`` replaced by ``P_k``)."""
+    N, C, H, Wh = layers.shape
+    W = full_width(Wh, W)
+    wy, wx = half_grid(H, W)
+    Pb = np.asarray(Pb, np.float64)
+    S = np.zeros((C, H * Wh), np.complex128)
+    for k in range(N):
+        S += np.exp(2j * np.pi * (Pb[k, 0] * wx + Pb[k, 1] * wy))[None] * layers[k].reshape(C, -1)
+    return image_from_half(S.reshape(C, H, Wh), W)
+
+
+def calib_loss_grad_shifts(b, wy, wx, P, lam: float, reg: int = REG_LAYER2):
+    """Eq. CalibrationProb over the listed bins with free shifts ``P [K][N][2]`` and its gradient
+    ``dL/dP [K][N][2]`` by Eq. gradP: ``4 pi sum_{q,c} w_a Im(r_j conj(A_jk) conj(x_k))``
+    (the relaxed model calibrates P directly).  ``reg`` must not depend on d."""
+    if reg == REG_VIEW2:
+        raise ValueError("the calibration gradient needs a regulariser independent of d")
+    P = np.asarray(P, np.float64)
+    wy = np.atleast_1d(np.asarray(wy, np.float64))
+    wx = np.atleast_1d(np.asarray(wx, np.float64))
+    N = P.shape[1]
+    A = system_matrix_general(wy, wx, P)
+    R = regulariser(reg, np.zeros(N), wy, wx, 0.0)
+    x = solve_system(b, A, lam, R)
+    r = A @ x - b
+    loss = np.sum(np.abs(r) ** 2) + lam * np.real(np.einsum("qkc,qkl,qlc->", np.conj(x), R, x))
+    core = np.imag(np.einsum("qjc,qjk,qkc->qjk", r, np.conj(A), np.conj(x)))
+    g = np.stack([4 * np.pi * np.einsum("q,qjk->jk", wx, core), 4 * np.pi * np.einsum("q,qjk->jk", wy, core)], -1)
+    return float(loss), g
