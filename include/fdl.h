@@ -220,6 +220,47 @@ FDL_API size_t fdl_aperture_table_workspace_size(int P, int Z);
 FDL_API int fdl_aperture_table(const float* raster, int P, int Z, float* table, void* workspace,
                                size_t workspace_bytes, void* stream);
 
+/* ---- the general system (Eq. AMatGeneral) ------------------------------ */
+/* Images j of any kind (Sec. V: "the model of Eq. refocus"): a sub-aperture
+ * view, an image with its own aperture psi_j and focus s_j (focal stacks,
+ * hybrid captures), and shifts either u_j d_k or free P_jk (the relaxed FDL
+ * model of the denoising application, which drops the rank-1 constraint
+ * P = u d^T):  A_jk = exp(+2 pi i P_jk . w) psi_hat_j((s_j - d_k) w). */
+typedef struct fdl_system {
+  const float* u;           /* DEVICE float32 [K][2] view positions (with d), or NULL with P */
+  const float* d;           /* DEVICE float32 [N] layer disparities: the shifts u_j d_k (without P),
+                               the view regulariser and the aperture argument (s_j - d_k) w */
+  const float* P;           /* DEVICE float32 [K][N][2] free shifts (x, y) in pixels, or NULL */
+  const fdl_request* views; /* DEVICE [K]: aperture, radius, s, pts, npts of each image, or NULL
+                               (every image a sub-aperture view); other fields ignored       */
+} fdl_system;
+
+/* Layer construction (Eq. LayerConstructionClosedForm) for the general system from
+ * half spectra [K][C][H][W/2+1], with the shared-memory solver at every
+ * frequency: native FP64 for FDL_PREC_F64, double-float otherwise (no tiers).
+ * Needs P or both u and d; views and FDL_REG_VIEW2 need d.  N <= 64. */
+FDL_API size_t fdl_fit_general_workspace_size(int K, int C, int H, int W, int N);
+FDL_API int fdl_fit_general(const float* spectra, int K, int C, int H, int W, int N,
+                            const fdl_system* sys, const fdl_fit_opts* opts, float* layers,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
+/* Images rendered with per-layer shifts (the relaxed model: an input view j is
+ * rendered with P_jk instead of u_j d_k; pinhole).  P: DEVICE float32 [B][N][2]
+ * (the shifts of output image b); out: DEVICE float32 [B][C][H][W]. */
+FDL_API size_t fdl_render_shifts_workspace_size(int B, int C, int H, int W);
+FDL_API int fdl_render_shifts(const float* layers, const float* P, int N, int C, int H, int W, int B,
+                              float* out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* The calibration objective over bins (as fdl_calib_grad) with free shifts P
+ * [K][N][2] and its gradient grad_P = dloss/dP [K][N][2] by Eq. gradP (the
+ * relaxed model searches P directly).  reg must be FDL_REG_LAYER2 or FDL_REG_L2;
+ * FDL_ENOTSUP when (1 + 2 K N) doubles plus the solver's matrices exceed the
+ * shared memory of one block (about K N <= 10,000). */
+FDL_API size_t fdl_calib_grad_shifts_workspace_size(int K, int C, int H, int W, int N, int nbins);
+FDL_API int fdl_calib_grad_shifts(const float* spectra, int K, int C, int H, int W, const float* P, int N,
+                                  const fdl_fit_opts* opts, const int* bins, int nbins, float* loss,
+                                  float* grad_P, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- calibration (Sec. V-B) ------------------------------------------- */
 
 /* Over the frequencies listed in bins (DEVICE int [nbins], flattened index

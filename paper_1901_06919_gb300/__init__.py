@@ -10,13 +10,17 @@ from .fdl import (  # noqa: F401
     RenderSpec,
     aperture_table,
     calib_grad,
+    calib_grad_shifts,
     fit,
+    fit_general,
     fit_spectra,
     irfft2,
     pack_requests,
+    pack_views,
     refocus,
     refocus_specs,
     render,
+    render_shifts,
     rfft2,
     workspace,
 )

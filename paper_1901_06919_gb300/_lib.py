@@ -40,6 +40,11 @@ class FdlError(RuntimeError):
 _lib = None
 
 # (name, restype, argtypes)
+class System(ct.Structure):
+    """fdl_system: device pointers (0 for NULL)."""
+    _fields_ = [("u", ct.c_void_p), ("d", ct.c_void_p), ("P", ct.c_void_p), ("views", ct.c_void_p)]
+
+
 _SIGS = [
     ("fdl_strerror", ct.c_char_p, [ct.c_int]),
     ("fdl_version", ct.c_int, []),
@@ -64,6 +69,18 @@ _SIGS = [
                               ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p]),
     ("fdl_refocus_workspace_size", ct.c_size_t, [ct.c_int] * 4),
     ("fdl_aperture_table_workspace_size", ct.c_size_t, [ct.c_int] * 2),
+    ("fdl_fit_general_workspace_size", ct.c_size_t, [ct.c_int] * 5),
+    ("fdl_fit_general", ct.c_int, [ct.c_void_p] + [ct.c_int] * 5 + [ct.POINTER(System), ct.POINTER(FitOpts),
+                                                                   ct.c_void_p, ct.c_void_p, ct.c_size_t,
+                                                                   ct.c_void_p]),
+    ("fdl_render_shifts_workspace_size", ct.c_size_t, [ct.c_int] * 4),
+    ("fdl_render_shifts", ct.c_int, [ct.c_void_p, ct.c_void_p] + [ct.c_int] * 5 + [ct.c_void_p, ct.c_void_p,
+                                                                                    ct.c_size_t, ct.c_void_p]),
+    ("fdl_calib_grad_shifts_workspace_size", ct.c_size_t, [ct.c_int] * 6),
+    ("fdl_calib_grad_shifts", ct.c_int, [ct.c_void_p] + [ct.c_int] * 4 + [ct.c_void_p, ct.c_int, ct.POINTER(FitOpts),
+                                                                          ct.c_void_p, ct.c_int, ct.c_void_p,
+                                                                          ct.c_void_p, ct.c_void_p, ct.c_size_t,
+                                                                          ct.c_void_p]),
     ("fdl_aperture_table", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_size_t,
                                       ct.c_void_p]),
     ("fdl_refocus", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int,

@@ -80,3 +80,52 @@ def calibrate(spectra: torch.Tensor, u0: torch.Tensor, d0: torch.Tensor, lam: fl
     out.u = u.detach()
     out.d = d.detach()
     return out
+
+
+class CalibLossShifts(torch.autograd.Function):
+    """loss(P) of Eq. CalibrationProb with free shifts P [K][N][2]; backward: dL/dP of Eq. gradP."""
+
+    @staticmethod
+    def forward(ctx, P, spectra, lam, reg, bins, precision):
+        loss, gP = fdl.calib_grad_shifts(spectra, P.detach().contiguous(), lam, reg=reg, bins=bins,
+                                         precision=precision)
+        ctx.save_for_backward(gP)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (gP,) = ctx.saved_tensors
+        return g * gP, None, None, None, None, None
+
+
+@dataclass
+class ShiftCalibResult:
+    P: torch.Tensor
+    losses: list = field(default_factory=list)
+
+
+def calibrate_shifts(spectra: torch.Tensor, P0: torch.Tensor, lam: float = 1e-2, steps: int = 200, lr: float = 1e-2,
+                     subset: int | None = 4096, seed: int = 0, reg: str = "layer2",
+                     precision: str = "df") -> ShiftCalibResult:
+    """The relaxed FDL model: the shifts P [K][N][2] searched directly (no rank-1 constraint
+    P = u d^T) by gradient descent with dL/dP, from ``P0`` (normally the rank-1 solution of
+    :func:`calibrate`, as the paper initialises it), on seeded frequency subsets, Adam steps."""
+    dev = spectra.device
+    K, C, H, Wh = spectra.shape
+    nbins = H * Wh
+    P = P0.detach().clone().to(dev).contiguous().requires_grad_(True)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    opt = torch.optim.Adam([P], lr=lr, betas=(0.9, 0.999))
+    out = ShiftCalibResult(P)
+    for _ in range(steps):
+        bins = None
+        if subset is not None and subset < nbins:
+            bins = torch.randperm(nbins, generator=gen, device=dev)[:subset].to(torch.int32)
+        loss = CalibLossShifts.apply(P, spectra, lam, reg, bins, precision)
+        opt.zero_grad(set_to_none=True)
+        loss.backward()
+        opt.step()
+        out.losses.append(float(loss.detach()))
+    out.P = P.detach()
+    return out

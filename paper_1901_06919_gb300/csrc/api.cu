@@ -507,6 +507,126 @@ FDL_API int fdl_calib_grad(const float* spectra, int K, int C, int H, int W, con
   return cuda_status(e);
 }
 
+// ------------------------------------------------------------------ general system
+FDL_API size_t fdl_fit_general_workspace_size(int K, int C, int H, int W, int N) {
+  if (K < 1 || C < 1 || N < 1 || !shape_ok(H, W)) return 0;
+  return carve_fit(nullptr, K, C, H, W, false).bytes;
+}
+
+FDL_API int fdl_fit_general(const float* spectra, int K, int C, int H, int W, int N, const fdl_system* sys,
+                            const fdl_fit_opts* opts, float* layers, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+  int s = check_fit_args(K, C, H, W, N, opts);
+  if (s != FDL_OK && s != FDL_ENOTSUP) return s;
+  if (!spectra || !sys || !layers || !workspace) return FDL_EINVAL;
+  if (!sys->P && !(sys->u && sys->d)) return FDL_EINVAL;
+  if ((sys->views || opts->reg == FDL_REG_VIEW2) && !sys->d) return FDL_EINVAL;
+  if (workspace_bytes < fdl_fit_general_workspace_size(K, C, H, W, N)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FitWs f = carve_fit(workspace, K, C, H, W, false);
+  SolveParams p{};
+  p.b = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
+  p.x = reinterpret_cast<float2*>(layers);
+  p.u = sys->u;
+  p.d = sys->d;
+  p.P = sys->P;
+  p.views = sys->views;
+  p.K = K;
+  p.C = C;
+  p.N = N;
+  p.H = H;
+  p.W = W;
+  p.reg = opts->reg;
+  p.lam = (float)opts->lambda;
+  p.lam_eps = (float)(opts->lambda * (opts->reg == FDL_REG_VIEW2 ? opts->eps : 0.0));
+  p.lam_d = opts->lambda;
+  p.lam_eps_d = opts->lambda * (opts->reg == FDL_REG_VIEW2 ? opts->eps : 0.0);
+  p.flagged = f.flagged;
+  p.flagged64 = f.flagged64;
+  p.counters = f.counters;
+  p.exp_table = f.exp_table;
+  p.mom = nullptr;
+  cudaError_t e = cudaMemsetAsync(f.counters, 0, 16 * sizeof(int), st);
+  if (e == cudaSuccess) e = launch_exp_table(f.exp_table, st);
+  if (e == cudaSuccess) e = launch_solve_hp(p, true, opts->precision == FDL_PREC_F64, 0, st);
+  return cuda_status(e);
+}
+
+FDL_API size_t fdl_render_shifts_workspace_size(int B, int C, int H, int W) {
+  if (B < 1 || C < 1 || C > 4 || !shape_ok(H, W)) return 0;
+  return render_ws_bytes(B, C, H, W, true);
+}
+
+FDL_API int fdl_render_shifts(const float* layers, const float* P, int N, int C, int H, int W, int B, float* out,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  if (B < 1 || C < 1 || C > 4 || N < 1 || N > 64 || !shape_ok(H, W)) return FDL_EINVAL;
+  if (!layers || !P || !out || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_render_shifts_workspace_size(B, C, H, W)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(workspace);
+  fdl_request* req = cv.take<fdl_request>(B);
+  float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
+  float2* nyq = cv.take<float2>((size_t)B * C * H);
+  float4* tables = cv.take<float4>(inv_table_elems(H, W));
+  // pinhole requests on the FDL (d unused: the shifts replace u0 d_k)
+  cudaError_t e = launch_pinhole_requests(req, layers, P, N, nullptr, B, out, (long long)C * H * W, st);
+  if (e == cudaSuccess)
+    e = launch_render_spectra(req, B, nullptr, C, H, W, N, render_spec_view(main, nyq, H, W), st, P);
+  if (e == cudaSuccess) e = render_inverse(main, nyq, tables, B, C, H, W, out, nullptr, nullptr, st);
+  return cuda_status(e);
+}
+
+FDL_API size_t fdl_calib_grad_shifts_workspace_size(int K, int C, int H, int W, int N, int nbins) {
+  (void)C;
+  (void)H;
+  (void)W;
+  (void)nbins;
+  if (K < 1 || N < 1) return 0;
+  return align_up(1024 * sizeof(float4)) + align_up((size_t)kCalibGrid * (1 + 2 * (size_t)K * N) * sizeof(double));
+}
+
+FDL_API int fdl_calib_grad_shifts(const float* spectra, int K, int C, int H, int W, const float* P, int N,
+                                  const fdl_fit_opts* opts, const int* bins, int nbins, float* loss, float* grad_P,
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+  int s = check_fit_args(K, C, H, W, N, opts);
+  if (s != FDL_OK && s != FDL_ENOTSUP) return s;
+  if (opts->reg == FDL_REG_VIEW2) return FDL_EINVAL;
+  if (!spectra || !P || !loss || !grad_P || !workspace) return FDL_EINVAL;
+  if (bins && nbins < 1) return FDL_EINVAL;
+  // one block holds the FP64 solver's matrices and the 1 + 2 K N accumulators
+  const size_t smem = (size_t)(N * (N + 1) + N + N * C + 4) * 16 + calib_shifts_acc_bytes(K, N);
+  if (smem > 200 * 1024) return FDL_ENOTSUP;
+  if (workspace_bytes < fdl_calib_grad_shifts_workspace_size(K, C, H, W, N, nbins)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver cv(workspace);
+  CalibParams p;
+  p.exp_table = cv.take<float4>(1024);
+  p.partials = cv.take<double>((size_t)kCalibGrid * (1 + 2 * (size_t)K * N));
+  p.b = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
+  p.u = nullptr;
+  p.d = nullptr;
+  p.P = P;
+  p.K = K;
+  p.C = C;
+  p.N = N;
+  p.H = H;
+  p.W = W;
+  p.reg = opts->reg;
+  p.lam = (float)opts->lambda;
+  p.lam_d = opts->lambda;
+  p.bins = bins;
+  p.nbins = bins ? nbins : 0;
+  p.loss = loss;
+  p.grad_u = nullptr;
+  p.grad_d = nullptr;
+  p.grad_P = grad_P;
+  p.counters = nullptr;
+  p.f64 = opts->precision == FDL_PREC_F64;
+  cudaError_t e = launch_exp_table(const_cast<float4*>(p.exp_table), st);
+  if (e == cudaSuccess) e = launch_calib_grad(p, st);
+  return cuda_status(e);
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ fixed-scratch fit

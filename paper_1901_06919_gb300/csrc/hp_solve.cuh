@@ -134,7 +134,83 @@ struct HpProblem {
   const float4* exp_table;
   int K, C, N, H, W, reg;
   double lam, lam_eps;
+  const float* P = nullptr;             // free shifts [K][N][2] (the relaxed model) or null: u_j d_k
+  const fdl_request* views = nullptr;   // per-image aperture and focus [K] or null: psi = delta
 };
+
+// psi_hat_j((s_j - d_k) w) of an image's aperture (Eq. AMatGeneral) in double: the closed
+// forms of the disc (J1), the square (sinc) and a point set; a drawn-aperture table by
+// bilinear interpolation of its FP32 entries.  wx, wy: the frequency in double.
+__device__ __forceinline__ void view_aperture(const fdl_request& v, float dk, double wy, double wx, double& re,
+                                              double& im) {
+  re = 1.0;
+  im = 0.0;
+  const double sd = (double)v.s - (double)dk;
+  const double nuy = sd * wy, nux = sd * wx;
+  if (v.aperture == FDL_AP_POINTS) {
+    double ar = 0.0, ai = 0.0;
+    for (int m = 0; m < v.npts; ++m) {
+      const double px = (double)__ldg(v.pts + 2 * m), py = (double)__ldg(v.pts + 2 * m + 1);
+      double sn, cs;
+      sincospi(-2.0 * (px * nux + py * nuy), &sn, &cs);
+      ar += cs;
+      ai += sn;
+    }
+    re = v.npts > 0 ? ar / v.npts : 0.0;
+    im = v.npts > 0 ? ai / v.npts : 0.0;
+    return;
+  }
+  if (v.aperture == FDL_AP_TABLE) {
+    const int Z = v.npts;
+    if (Z < 1) return;
+    const float2* T = reinterpret_cast<const float2*>(v.pts);
+    double gy = nuy * Z * (double)v.radius, gx = nux * Z * (double)v.radius;
+    if (!(fabs(gy) < 1e30) || !(fabs(gx) < 1e30)) {
+      re = 0.0;
+      return;
+    }
+    gy -= Z * floor(gy / Z);
+    gx -= Z * floor(gx / Z);
+    const double y0f = fmin(floor(gy), (double)(Z - 1)), x0f = fmin(floor(gx), (double)(Z - 1));
+    const double fy = gy - y0f, fx = gx - x0f;
+    const int y0 = (int)y0f, x0 = (int)x0f;
+    const int Zh = Z / 2 + 1;
+    double acc_r = 0.0, acc_i = 0.0;
+    for (int t = 0; t < 4; ++t) {
+      int iy = y0 + (t >> 1), ix = x0 + (t & 1);
+      iy = iy >= Z ? iy - Z : iy;
+      ix = ix >= Z ? ix - Z : ix;
+      float2 e;
+      if (ix <= Z / 2) {
+        e = __ldg(T + (long long)iy * Zh + ix);
+      } else {
+        e = __ldg(T + (long long)(iy ? Z - iy : 0) * Zh + (Z - ix));
+        e.y = -e.y;
+      }
+      const double wgt = ((t >> 1) ? fy : 1.0 - fy) * ((t & 1) ? fx : 1.0 - fx);
+      acc_r += wgt * e.x;
+      acc_i += wgt * e.y;
+    }
+    re = acc_r;
+    im = acc_i;
+    return;
+  }
+  if (v.aperture == FDL_AP_PINHOLE || v.radius == 0.f) return;
+  if (v.aperture == FDL_AP_DISC) {
+    const double z = 6.283185307179586 * (double)v.radius * sqrt(nux * nux + nuy * nuy);
+    re = z < 1e-8 ? 1.0 - 0.125 * z * z : 2.0 * j1(z) / z;
+    return;
+  }
+  // square of half side r
+  const double sx = 2.0 * (double)v.radius * nux, sy = 2.0 * (double)v.radius * nuy;
+  const double fx = sx == 0.0 ? 1.0 : sinpi(sx) / (3.141592653589793 * sx);
+  const double fy = sy == 0.0 ? 1.0 : sinpi(sy) / (3.141592653589793 * sy);
+  re = fx * fy;
+}
+__device__ __forceinline__ double freq_x_double(const FreqD& f) { return f.wx; }
+__device__ __forceinline__ double freq_y_double(const FreqD& f) { return f.wy; }
+__device__ __forceinline__ double freq_x_double(const Freq& f) { return (double)f.wx + (double)f.wx_lo; }
+__device__ __forceinline__ double freq_y_double(const Freq& f) { return (double)f.wy + (double)f.wy_lo; }
 
 // Shared memory of one warp: G [N][N+1], Arow [N], Y [N][C] (cx<T>).
 template <class T>
@@ -157,9 +233,24 @@ __device__ bool hp_solve_bin(const HpProblem& p, int ky, int kx, cx<T>* G, cx<T>
   for (int e = lane; e < N * C; e += 32) Y[e] = {zero, zero};
   __syncwarp();
   for (int j = 0; j < p.K; ++j) {
-    const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
-    const auto th = theta_r(uj.x, uj.y, fq, T{});
-    for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(phase_r(th, __ldg(p.d + r)), p.exp_table);
+    if (p.P == nullptr) {
+      const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
+      const auto th = theta_r(uj.x, uj.y, fq, T{});
+      for (int r = lane; r < N; r += 32) Arow[r] = cexp2pi(phase_r(th, __ldg(p.d + r)), p.exp_table);
+    } else {
+      for (int r = lane; r < N; r += 32) {
+        const float2 pr = __ldg(reinterpret_cast<const float2*>(p.P) + (long long)j * N + r);
+        Arow[r] = cexp2pi(phase_r(theta_r(pr.x, pr.y, fq, T{}), 1.f), p.exp_table);
+      }
+    }
+    if (p.views != nullptr) {
+      const fdl_request v = p.views[j];
+      for (int r = lane; r < N; r += 32) {
+        double ar, ai;
+        view_aperture(v, __ldg(p.d + r), freq_y_double(fq), freq_x_double(fq), ar, ai);
+        Arow[r] = cx_mul(Arow[r], cx<T>{r_from_double(ar, T{}), r_from_double(ai, T{})});
+      }
+    }
     __syncwarp();
     float2 bj[4];
 #pragma unroll

@@ -59,6 +59,8 @@ struct SolveParams {
   int* counters;       // [0] FP32 bins, [1] double-float bins, [2] breakdowns, [3] non-finite,
                        // [4] double-float list length, [5] FP64 list length, [6] FP64 bins
   const float4* exp_table;  // df table of exp(2 pi i n / 1024), n in [0, 1024)
+  const float* P = nullptr;               // free shifts [K][N][2] (k_solve_hp only)
+  const fdl_request* views = nullptr;     // per-image apertures [K] (k_solve_hp only)
   // Moment form of the double-float Gram (nullable): kMomSlots float2, entries [0, N)
   // e_k = d_k - d_0 - k Delta as double-floats, written by the check kernel, which also
   // sets counters[8] to 1 when the moment form applies.
@@ -128,8 +130,10 @@ cudaError_t launch_select_budget(const float* err, const float* xn2, int n, doub
 // ---- render (render.cu) -----------------------------------------------------
 // Nmax: largest N of any request; sizes the shared layer tile used when all
 // requests read one FDL.
+// shifts: optional [B][N][2] per-layer shifts of each request (the relaxed model's P_jk
+// instead of u0 d_k; pinhole requests)
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                                  SpecView out, cudaStream_t st);
+                                  SpecView out, cudaStream_t st, const float* shifts = nullptr);
 // drawn aperture: centred zero-padded raster and its sum (double), then the table scaling
 cudaError_t launch_aperture_table_prep(const float* R, int P, int Z, float* pad, double* sum, cudaStream_t st);
 cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cudaStream_t st);
@@ -154,8 +158,12 @@ struct CalibParams {
   const float4* exp_table;
   bool f64;
   double lam_d;
+  const float* P = nullptr;  // free shifts [K][N][2]: dL/dP into grad_P instead of grad_u, grad_d
+  float* grad_P = nullptr;   // [K][N][2]
 };
 constexpr int kCalibGrid = 512;
 cudaError_t launch_calib_grad(const CalibParams& p, cudaStream_t st);
+// shared-memory accumulators of the free-shift gradient (one CTA): 1 + 2 K N doubles
+size_t calib_shifts_acc_bytes(int K, int N);
 
 }  // namespace fdl

@@ -81,15 +81,24 @@ constexpr int kTileMaxLC = 256;  // N * C of an FDL staged in shared memory
 
 // sum over layers k = k0, k0 + kstep, ... < r.N of the Eq. BsFourier terms of request r at
 // this lane's frequency; layer values from the shared tile when given, else from global
+// shb: this request's per-layer shifts P_k (the relaxed model) or null: u0 d_k
 __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                              float wx, float wabs, long long plane, long long off, bool valid,
-                                             const float2* tile, const float* dsh, int lane, float2 acc[4]) {
+                                             const float2* tile, const float* dsh, int lane, float2 acc[4],
+                                             const float2* __restrict__ shb, const Freq& fq) {
   const float2* x = reinterpret_cast<const float2*>(r.layers);
   const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
   for (int k = k0; k < r.N; k += kstep) {
     const float dk = tile ? dsh[k] : __ldg(r.d + k);
     float2 sh;
-    sincospif(2.f * phase_from_theta(theta, dk), &sh.y, &sh.x);
+    float ph;
+    if (shb != nullptr) {
+      const float2 pk = __ldg(shb + k);
+      ph = phase_cycles(pk.x, pk.y, fq, 1.f);
+    } else {
+      ph = phase_from_theta(theta, dk);
+    }
+    sincospif(2.f * ph, &sh.y, &sh.x);
     const float sd = r.s - dk;
     float2 coef = sh;
     if (r.aperture == FDL_AP_DISC && r.radius != 0.f) {
@@ -117,7 +126,7 @@ __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int k
 //    still occupies the whole CTA.
 __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request* __restrict__ req, int B,
                                                               const int* __restrict__ count, int C, int H, int W,
-                                                              int tile_lc, SpecView out) {
+                                                              int tile_lc, SpecView out, const float* __restrict__ shifts) {
   extern __shared__ float2 tile[];  // [tile_lc][32]
   __shared__ float dsh[64];
   __shared__ float2 part[kRenderWarps][4][32];
@@ -147,7 +156,8 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
     if (b < Bact) {
       const fdl_request r = req[b];
       const df theta = df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, wxlo, r.u0y * wylo));
-      render_terms(r, sl, G, C, theta, wy, wx, wabs, plane, off, valid, nullptr, nullptr, lane, acc);
+      const float2* shb = shifts ? reinterpret_cast<const float2*>(shifts) + (long long)b * r.N : nullptr;
+      render_terms(r, sl, G, C, theta, wy, wx, wabs, plane, off, valid, nullptr, nullptr, lane, acc, shb, fq);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) part[warp][c][lane] = acc[c];
@@ -194,7 +204,9 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
-    render_terms(r, 0, 1, C, theta, wy, wx, wabs, plane, off, valid, shared ? tile : nullptr, dsh, lane, acc);
+    const float2* shb = shifts ? reinterpret_cast<const float2*>(shifts) + (long long)b * r.N : nullptr;
+    render_terms(r, 0, 1, C, theta, wy, wx, wabs, plane, off, valid, shared ? tile : nullptr, dsh, lane, acc, shb,
+                 fq);
     if (valid) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
@@ -215,8 +227,8 @@ __global__ void k_pinhole_requests(fdl_request* req, const float* layers, const 
   r.N = N;
   r.npts = 0;
   r.aperture = FDL_AP_PINHOLE;
-  r.u0x = u0[2 * b];
-  r.u0y = u0[2 * b + 1];
+  r.u0x = u0 ? u0[2 * b] : 0.f;  // null: shifts given per layer instead
+  r.u0y = u0 ? u0[2 * b + 1] : 0.f;
   r.s = 0.f;
   r.radius = 0.f;
   r.pad_ = 0;
@@ -274,13 +286,13 @@ cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cud
 }
 
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                                  SpecView out, cudaStream_t st) {
+                                  SpecView out, cudaStream_t st, const float* shifts) {
   const int Qs = H * (W / 2 + 1);
   const int tile_lc = min(Nmax * C, kTileMaxLC);
   const size_t smem = (size_t)tile_lc * 32 * sizeof(float2);
   cudaError_t e = set_smem((const void*)k_render, (size_t)kTileMaxLC * 32 * sizeof(float2));
   if (e != cudaSuccess) return e;
-  k_render<<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, out);
+  k_render<<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, out, shifts);
   return cudaGetLastError();
 }
 

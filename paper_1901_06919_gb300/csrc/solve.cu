@@ -292,6 +292,8 @@ __global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, 
   p.reg = sp.reg;
   p.lam = sp.lam_d;
   p.lam_eps = sp.lam_eps_d;
+  p.P = sp.P;
+  p.views = sp.views;
   const int N = p.N, C = p.C;
   cx<T>* G = reinterpret_cast<cx<T>*>(smem4) + warp * hp_warp_elems<T>(N, C);
   cx<T>* Arow = G + N * (N + 1);

@@ -229,6 +229,83 @@ def refocus_specs(specs: list[RenderSpec], stream=None) -> list[torch.Tensor]:
     return [s.out for s in specs]
 
 
+# ---------------------------------------------------------------- general system
+def pack_views(views: list, device) -> torch.Tensor:
+    """Device ``fdl_request`` array describing each input image's aperture and focus for
+    :func:`fit_general`: entries ``(aperture, radius, s)`` or ``(aperture, radius, s, pts)``."""
+    arr = (L.Request * len(views))()
+    keep = []
+    for i, v in enumerate(views):
+        kind, radius, s = v[0], v[1], v[2]
+        pts = v[3] if len(v) > 3 else None
+        if pts is not None:
+            keep.append(pts)
+        npts = 0 if pts is None else pts.shape[0]
+        arr[i] = L.Request(None, None, None, pts.data_ptr() if pts is not None else None, 0, npts, L.APERTURE[kind],
+                           0.0, 0.0, float(s), float(radius), 0)
+    return torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(device)
+
+
+def fit_general(spectra: torch.Tensor, N: int, lam: float, eps: float = 1e-4, reg: str = "view2",
+                precision: str = "df", u: torch.Tensor | None = None, d: torch.Tensor | None = None,
+                P: torch.Tensor | None = None, views: torch.Tensor | None = None, W: int | None = None,
+                stream=None) -> torch.Tensor:
+    """Layer construction for the general system of Eq. AMatGeneral: shifts ``u_j d_k`` or free
+    ``P [K][N][2]`` (the relaxed model), per-image apertures from :func:`pack_views` (focal
+    stacks, hybrid inputs).  ``precision``: "f64" or double-float."""
+    _need(spectra, torch.complex64, "spectra", 4)
+    for t, name in ((u, "u"), (d, "d"), (P, "P")):
+        if t is not None:
+            _need(t, torch.float32, name)
+    K, C, H, Wh = spectra.shape
+    W = _width(Wh, W)
+    lib = _lib()
+    out = torch.empty((N, C, H, Wh), dtype=torch.complex64, device=spectra.device)
+    ws = workspace(lib.fdl_fit_general_workspace_size(K, C, H, W, N), spectra.device)
+    sysd = L.System(_p(u).value, _p(d).value, _p(P).value, _p(views).value)
+    o = _opts(lam, eps, reg, precision, 0.0)
+    L.check(lib.fdl_fit_general(_p(spectra), K, C, H, W, N, ct.byref(sysd), ct.byref(o), _p(out), _p(ws),
+                                ws.numel(), _stream(stream)), "fdl_fit_general")
+    return out
+
+
+def render_shifts(layers: torch.Tensor, P: torch.Tensor, W: int | None = None, stream=None) -> torch.Tensor:
+    """Images ``[B][C][H][W]`` rendered with per-layer shifts ``P [B][N][2]`` (the relaxed model)."""
+    _need(layers, torch.complex64, "layers", 4)
+    _need(P, torch.float32, "P", 3)
+    N, C, H, Wh = layers.shape
+    W = _width(Wh, W)
+    B = P.shape[0]
+    lib = _lib()
+    out = torch.empty((B, C, H, W), dtype=torch.float32, device=layers.device)
+    ws = workspace(lib.fdl_render_shifts_workspace_size(B, C, H, W), layers.device)
+    L.check(lib.fdl_render_shifts(_p(layers), _p(P), N, C, H, W, B, _p(out), _p(ws), ws.numel(), _stream(stream)),
+            "fdl_render_shifts")
+    return out
+
+
+def calib_grad_shifts(spectra: torch.Tensor, P: torch.Tensor, lam: float, reg: str = "layer2",
+                      bins: torch.Tensor | None = None, precision: str = "df", W: int | None = None, stream=None):
+    """Loss of Eq. CalibrationProb with free shifts ``P [K][N][2]`` and ``dL/dP`` (Eq. gradP)."""
+    _need(spectra, torch.complex64, "spectra", 4)
+    _need(P, torch.float32, "P", 3)
+    K, C, H, Wh = spectra.shape
+    W = _width(Wh, W)
+    N = P.shape[1]
+    nb = 0
+    if bins is not None:
+        _need(bins, torch.int32, "bins", 1)
+        nb = bins.numel()
+    lib = _lib()
+    loss = torch.empty(1, dtype=torch.float32, device=spectra.device)
+    gP = torch.empty((K, N, 2), dtype=torch.float32, device=spectra.device)
+    ws = workspace(lib.fdl_calib_grad_shifts_workspace_size(K, C, H, W, N, nb), spectra.device)
+    o = _opts(lam, 0.0, reg, precision, 0.0)
+    L.check(lib.fdl_calib_grad_shifts(_p(spectra), K, C, H, W, _p(P), N, ct.byref(o), _p(bins), nb, _p(loss),
+                                      _p(gP), _p(ws), ws.numel(), _stream(stream)), "fdl_calib_grad_shifts")
+    return loss, gP
+
+
 # ---------------------------------------------------------------- calibration
 def calib_grad(spectra: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, reg: str = "layer2",
                bins: torch.Tensor | None = None, precision: str = "df", stream=None, W: int | None = None):
