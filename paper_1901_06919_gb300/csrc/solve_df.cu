@@ -267,12 +267,22 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
     df T1 = {0.f, 0.f};
     float T2 = 0.f, T3 = 0.f;
 
+    // this frequency's K*C inputs staged in the (still unused) factor region, all lanes
+    // loading at once, when they fit: one memory latency per frequency instead of per view
+    const bool stage = K * C <= NMAX * (NMAX + 1);
+    float2* bst = reinterpret_cast<float2*>(Ls);
+    if (stage) {
+      for (int e = lane; e < K * C; e += 32) bst[e] = *p.b.at(e, ky, kx, M);
+      __syncwarp();
+    }
+
     for (int j = 0; j < K; ++j) {
       const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
       const ThetaX th = theta_r(uj.x, uj.y, fq, Rdf{});
       float2 bj[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bj[c] = c < C ? *p.b.at((long long)j * C + c, ky, kx, M) : make_float2(0.f, 0.f);
+      for (int c = 0; c < 4; ++c)
+        bj[c] = c < C ? (stage ? bst[j * C + c] : *p.b.at((long long)j * C + c, ky, kx, M)) : make_float2(0.f, 0.f);
       dfc aR[R];  // A_jr of this lane's rows (moment form)
 #pragma unroll
       for (int h = 0; h < R; ++h) {
