@@ -124,11 +124,31 @@ __device__ __forceinline__ void sub_conj_mul(dfc& g, const dfc& a, const dfc& b)
 
 __device__ __forceinline__ dfc scale(const dfc& a, df s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
 
-// y += conj(a) * b for a double-float (re.hi, im.hi, re.lo, im.lo), b single precision
+// y += conj(a) * b for a double-float (re.hi, im.hi, re.lo, im.lo), b single precision:
+// the products of the high words exact (TwoProd), their sums by TwoSum, every rounding
+// error and the low-word products collected in the low word, which is left
+// unnormalised (renormalised once after the view loop)
 __device__ __forceinline__ void rhs_acc(dfc& y, float4 a, float2 b) {
-  const df are = {a.x, a.z}, aim = {a.y, a.w}, br = {b.x, 0.f}, bi = {b.y, 0.f};
-  y.re = acc2(y.re, mul3(are, br), mul3(aim, bi));
-  y.im = acc2(y.im, mul3(are, bi), neg3(mul3(aim, br)));
+  {  // re += a.re b.x + a.im b.y
+    const float p1 = __fmul_rn(a.x, b.x), e1 = fmaf(a.x, b.x, -p1);
+    const float p2 = __fmul_rn(a.y, b.y), e2 = fmaf(a.y, b.y, -p2);
+    const df s1 = two_sum(y.re.hi, p1);
+    const df s2 = two_sum(s1.hi, p2);
+    float lo = y.re.lo + (s1.lo + s2.lo) + (e1 + e2);
+    lo = fmaf(a.z, b.x, lo);
+    lo = fmaf(a.w, b.y, lo);
+    y.re = {s2.hi, lo};
+  }
+  {  // im += a.re b.y - a.im b.x
+    const float p1 = __fmul_rn(a.x, b.y), e1 = fmaf(a.x, b.y, -p1);
+    const float p2 = __fmul_rn(a.y, b.x), e2 = fmaf(a.y, b.x, -p2);
+    const df s1 = two_sum(y.im.hi, p1);
+    const df s2 = two_sum(s1.hi, -p2);
+    float lo = y.im.lo + (s1.lo + s2.lo) + (e1 - e2);
+    lo = fmaf(a.z, b.y, lo);
+    lo = fmaf(-a.w, b.x, lo);
+    y.im = {s2.hi, lo};
+  }
 }
 
 __device__ __forceinline__ float4 shfl4(float4 v, int src) {
@@ -416,6 +436,11 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
         }
       }
     }
+    // the right-hand sides were accumulated with unnormalised low words
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) renorm(y[h][c]);
     // sum_j b_j per channel: lanes over views, then a butterfly of double-float adds
     {
       dfc bs[4];
