@@ -843,6 +843,12 @@ def moment_form_applies(u, d):
 # Gram 14.6k, A 14.6k, right-hand side 58.3k, Cholesky 36k, solves 21.6k.
 SURVEY_FLOPS_PER_FREQUENCY = 145_000
 
+# DRAM bytes (read + write) per frequency of k_solve_df<30, 15, moment form>, from one ncu capture
+# of the mixed fit's double-float launch on this workload (74,398 listed frequencies: 158.05 MB
+# read, 39.60 MB written).  The algorithmic bytes are the K x C spectrum values read and the
+# N x C layer values written, 8 bytes each: 2,664 per frequency.
+DF_DRAM_BYTES_PER_FREQUENCY = (158.046464e6 + 39.597312e6) / 74_398
+
 
 def roofline_entry(legs, clk, moment):
     """The dominant kernel is the double-float solve (launch list); it is bound by the FP32 pipe."""
@@ -854,7 +860,10 @@ def roofline_entry(legs, clk, moment):
     form = "moment-form Gram" if moment else "direct Gram"
     return {"kernel": f"k_solve_df (double-float per-frequency solve, {form}, all 131,584 frequencies)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFP32op/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": DF_DRAM_BYTES_PER_FREQUENCY * q_half() if moment else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                            "scaled from the 74,398-frequency launch to all frequencies)",
+            "algorithmic_bytes": ((2 * GRID + 1) ** 2 + N) * C * 8 * q_half(),
             "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock sampled in the run)",
             "work_per_frequency_fp32_ops": per_q,
             "fp32_method_flops_per_frequency": SURVEY_FLOPS_PER_FREQUENCY,
