@@ -11,7 +11,13 @@
 //    products exactly (TwoProd), adds them with TwoSum and collects every
 //    rounding error, plus the hi*lo cross terms, in the low word;
 //  * Cholesky runs on the register slots with the pivot column broadcast
-//    through shared memory; the triangular solves run one row per lane.
+//    through shared memory.  The right-hand sides ride along as N*C extra slots
+//    (row-major (k, c) numbering), so the factorisation also performs the forward
+//    substitution L z = A*b.  Both numberings put the entries still to be
+//    updated at pivot k in the trailing slots, so the update loop runs from the
+//    last slot down and stops at the first slot that holds nothing beyond
+//    column (row) k; the entries left behind are final and no longer read from
+//    registers.  The back substitution runs one row per lane.
 //
 // Moment form of the Gram matrix (MOM = true).  G_rl = sum_j exp(2 pi i (d_l - d_r)
 // theta_j) depends on the pair only through d_l - d_r.  Writing d_k = d_0 + k Delta + e_k
@@ -37,6 +43,11 @@ constexpr int kDfWarps = 4;
 // light fields, all frequencies in double-float (N = 16: 7.8 / 6.2 / 5.7 ms with 2 / 3 / 4;
 // N = 30: 23.6 / 19.7 / 23.6 ms; N = 40: 41.5 / 66.3 / 69.5 ms, where spills dominate).
 constexpr int df_min_blocks(int nmax) { return nmax <= 16 ? 4 : (nmax <= 32 ? 3 : 2); }
+
+// float4 words of shared memory per warp: A_j / next pivot column and the current column
+// (NMAX + 1 each), the packed factor, [NMAX][4] right-hand sides, 2 x 4 pivot-row values,
+// NMAX double-float reciprocals
+__host__ __device__ constexpr int df_warp_f4(int nmax) { return 2 * (nmax + 1) + nmax * (nmax + 1) / 2 + 4 * nmax + 8 + (nmax + 1) / 2; }
 
 // entry (r, l), l <= r, numbered column-major: column l starts at l*N - l(l-1)/2
 __device__ __forceinline__ int col_start(int l, int N) { return l * N - (l * (l - 1)) / 2; }
@@ -221,10 +232,14 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int N = p.N, C = p.C, K = p.K, M = p.W >> 1;
   const int E = N * (N + 1) / 2;
-  float4* Arow = sm4 + warp * (2 * NMAX + NMAX * (NMAX + 1) / 2 + NMAX);
-  float4* col = Arow + NMAX;
-  float4* Ls = col + NMAX;                       // packed lower triangle, column-major
-  float2* invd = reinterpret_cast<float2*>(Ls + NMAX * (NMAX + 1) / 2);  // 1 / L_kk as df
+  constexpr int SY = (4 * NMAX + 31) / 32;  // right-hand-side slots per lane (C <= 4)
+  float4* Arow = sm4 + warp * df_warp_f4(NMAX);  // A_j of one view; the next pivot column in the factorisation
+  float4* col = Arow + NMAX + 1;                 // the current column of L
+  float4* Ls = col + NMAX + 1;                   // packed lower triangle, column-major
+  float4* zbuf = Ls + NMAX * (NMAX + 1) / 2;     // [N][C] right-hand sides, then z = L^-1 A*b
+  float4* ynext = zbuf + 4 * NMAX;               // [C] right-hand sides of the next pivot row
+  float4* zc = ynext + 4;                        // [C] z of the current pivot row
+  float2* invd = reinterpret_cast<float2*>(zc + 4);  // 1 / L_kk as df
 
   // coordinates (r, l) of this lane's slots, packed as r * 256 + l.  An unused slot
   // (entry number >= E) gets (N, N): it reads Arow[N] / col[N], which lie inside this
@@ -241,10 +256,17 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
       rl[s] = ((l + (e - col_start(l, N))) << 8) | l;
     }
   }
+  // right-hand-side slots: entry i = k * C + c (layer k, channel c) in lane i % 32,
+  // slot i / 32, packed as k * 256 + c; unused ones get layer N (col[N] stays zero)
+  int yk[SY];
+#pragma unroll
+  for (int t = 0; t < SY; ++t) {
+    const int i = lane + 32 * t;
+    yk[t] = (i < N * C) ? (((i / C) << 8) | (i % C)) : (N << 8);
+  }
 #define SR(s) (rl[s] >> 8)
 #define SL(s) (rl[s] & 255)
-#define SLOT_USED(s) (lane + 32 * (s) < E)
-  for (int i = lane; i < 2 * NMAX + 1; i += 32) Arow[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = lane; i < 2 * (NMAX + 1); i += 32) Arow[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
   float2 em[R];  // e_m of this lane's moments (moment form)
 #pragma unroll
@@ -315,8 +337,8 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
           const df t = two_sum(a.re.v.hi, -1.f);
           const df am = two_sum(t.hi, __fadd_rn(t.lo, a.re.v.lo));
           const float4 av = make_float4(am.hi, a.im.v.hi, am.lo, a.im.v.lo);
-          Arow[r] = av;
           if constexpr (!MOM) {
+            Arow[r] = av;
             const df s1 = two_sum(Ssum[h].re.hi, am.hi);
             Ssum[h].re = two_sum(s1.hi, __fadd_rn(__fadd_rn(Ssum[h].re.lo, s1.lo), am.lo));
             const df s2 = two_sum(Ssum[h].im.hi, a.im.v.hi);
@@ -354,7 +376,6 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
             M3[h].y = fmaf(th3, wi.hi, M3[h].y);
           }
         }
-        __syncwarp();
         continue;
       }
       __syncwarp();
@@ -508,44 +529,80 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
 
-    // Cholesky on the slots
+    // Cholesky with the right-hand sides as extra rows: the (N + c, k) entries of the
+    // factor of [[G, y], [y*, .]] are conj(z_kc), z = L^-1 y.  The right-hand sides
+    // move to their slots through shared memory.
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+      const int r = lane + 32 * h;
+      if (r < N)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < C) zbuf[r * C + c] = pack(y[h][c]);
+    }
+    __syncwarp();
+    dfc Y[SY];
+#pragma unroll
+    for (int t = 0; t < SY; ++t) {
+      const int i = lane + 32 * t;
+      Y[t] = i < N * C ? unpack(zbuf[i]) : dfc{{0.f, 0.f}, {0.f, 0.f}};
+    }
+    // column 0 and the right-hand sides of row 0 start the pivot sequence
+    if (lane < C) ynext[lane] = zbuf[lane];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (SL(s) == 0 && SR(s) < N) Arow[SR(s)] = pack(G[s]);
+    __syncwarp();
     bool ok = true;
     for (int k = 0; k < N; ++k) {
-      // the owner of (k, k) publishes the pivot
-#pragma unroll
-      for (int s = 0; s < S; ++s)
-        if (SR(s) == k && SL(s) == k) col[k] = make_float4(G[s].re.hi, 0.f, G[s].re.lo, 0.f);
-      __syncwarp();
-      const float4 pv = col[k];
+      // every lane takes the pivot, scales its rows of column k and publishes them
+      const float4 pv = Arow[k];
       const df piv = {pv.x, pv.z};
       ok = ok && (piv.hi > 0.f);
       const df lkk = df_sqrt(piv.hi > 0.f ? piv : df_from(1.f));
       const df inv = df_div(df_from(1.f), lkk);
+      const int ck = col_start(k, N);
+#pragma unroll
+      for (int h = 0; h < R; ++h) {
+        const int r = lane + 32 * h;
+        if (r >= k && r < N) {
+          const float4 v = r == k ? make_float4(lkk.hi, 0.f, lkk.lo, 0.f) : pack(scale(unpack(Arow[r]), inv));
+          col[r] = v;
+          Ls[ck + (r - k)] = v;
+        }
+      }
+      if (lane < C) {
+        const float4 z = pack(scale(unpack(ynext[lane]), inv));
+        zc[lane] = z;
+        zbuf[k * C + lane] = z;
+      }
       if (lane == 0) invd[k] = make_float2(inv.hi, inv.lo);
       __syncwarp();
-      // scale column k and publish it
+      if (k + 1 < N) {
+        // trailing update G_rl -= L_rk conj(L_lk) for l > k: the slots from the first one
+        // holding an entry of column k + 1 on; the entries of column k + 1 go to Arow
+        // for the next pivot
+        const int s0 = col_start(k + 1, N) >> 5;
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        if (SL(s) == k) {
-          if (SR(s) == k) {
-            G[s] = {lkk, {0.f, 0.f}};
-          } else {
-            G[s] = scale(G[s], inv);
-          }
-          col[SR(s)] = pack(G[s]);
+        for (int s = S - 1; s >= 0; --s) {
+          if (s < s0) break;
+          if (32 * s >= E) continue;  // unused slots (N < NMAX)
+          sub_mul_conj(G[s], unpack(col[SR(s)]), unpack(col[SL(s)]));
+          if (SL(s) == k + 1) Arow[SR(s)] = pack(G[s]);
+        }
+        // forward substitution y_rc -= L_rk z_kc for r > k
+        const int t0 = ((k + 1) * C) >> 5;
+#pragma unroll
+        for (int t = SY - 1; t >= 0; --t) {
+          if (t < t0) break;
+          if (32 * t >= N * C) continue;  // unused slots (C < 4)
+          const int r = yk[t] >> 8, c = yk[t] & 255;
+          sub_mul(Y[t], unpack(col[r]), unpack(zc[c]));
+          if (r == k + 1) ynext[c] = pack(Y[t]);
         }
       }
       __syncwarp();
-      // trailing update G_rl -= L_rk conj(L_lk), l > k
-#pragma unroll
-      for (int s = 0; s < S; ++s)
-        if (SL(s) > k) sub_mul_conj(G[s], unpack(col[SR(s)]), unpack(col[SL(s)]));
-      __syncwarp();
     }
-#pragma unroll
-    for (int s = 0; s < S; ++s)
-      if (SLOT_USED(s)) Ls[lane + 32 * s] = pack(G[s]);
-    __syncwarp();
 
     // Condition estimate kappa ~ trace(G) |G^-1 v| after three steps of inverse iteration
     // with the factor (FP32 is enough for an error estimate).
@@ -618,27 +675,13 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
       kappa = tr * vnorm;
     }
 
-    // forward substitution L z = y, row r in lane r % 32
-    for (int k = 0; k < N; ++k) {
-      const float2 iv = invd[k];
-      const df inv = {iv.x, iv.y};
-      const int owner = k & 31, hk = k >> 5;
+    // z = L^-1 A*b from the factorisation, one row per lane
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (c < C) {
-          float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int h = 0; h < R; ++h) {
+      const int r = lane + 32 * h;
 #pragma unroll
-          for (int h = 0; h < R; ++h)
-            if (h == hk) mine = pack(y[h][c]);
-          const dfc zk = scale(unpack(shfl4(mine, owner)), inv);
-#pragma unroll
-          for (int h = 0; h < R; ++h) {
-            const int r = lane + 32 * h;
-            if (r > k && r < N) sub_mul(y[h][c], unpack(Ls[col_start(k, N) + (r - k)]), zk);
-            else if (r == k) y[h][c] = zk;
-          }
-        }
-      }
+      for (int c = 0; c < 4; ++c)
+        if (c < C && r < N) y[h][c] = unpack(zbuf[r * C + c]);
     }
     // back substitution L* x = z
     for (int k = N - 1; k >= 0; --k) {
@@ -696,7 +739,6 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
   }
 #undef SR
 #undef SL
-#undef SLOT_USED
   if (lane == 0) {
     if (nhp) atomicAdd(p.counters + 1, nhp);
     // a listed frequency was first solved (and counted) by the FP32 pass
@@ -707,7 +749,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
 
 template <int NMAX, int S, bool MOM>
 cudaError_t launch_df_v(const SolveParams& p, bool all_bins, cudaStream_t st) {
-  const size_t per_warp = (size_t)(2 * NMAX + NMAX * (NMAX + 1) / 2 + NMAX) * sizeof(float4);
+  const size_t per_warp = (size_t)df_warp_f4(NMAX) * sizeof(float4);
   const size_t smem = per_warp * kDfWarps;
   cudaError_t e = set_smem((const void*)k_solve_df<NMAX, S, MOM>, smem);
   if (e != cudaSuccess) return e;
