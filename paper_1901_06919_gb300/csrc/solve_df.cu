@@ -17,7 +17,8 @@
 //    updated at pivot k in the trailing slots, so the update loop runs from the
 //    last slot down and stops at the first slot that holds nothing beyond
 //    column (row) k; the entries left behind are final and no longer read from
-//    registers.  The back substitution runs one row per lane.
+//    registers.  The back substitution L* x = z runs on the same right-hand-side
+//    slots, where the rows still open at step k are a prefix.
 //
 // Moment form of the Gram matrix (MOM = true).  G_rl = sum_j exp(2 pi i (d_l - d_r)
 // theta_j) depends on the pair only through d_l - d_r.  Writing d_k = d_0 + k Delta + e_k
@@ -675,36 +676,45 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
       kappa = tr * vnorm;
     }
 
-    // z = L^-1 A*b from the factorisation, one row per lane
+    // back substitution L* x = z on the right-hand-side slots: at step k the entries of
+    // the rows r < k (a prefix of the row-major numbering) take x_k; the entries of row
+    // k - 1 are then final and go to ynext for the next step; x_k goes to zbuf
+#pragma unroll
+    for (int t = 0; t < SY; ++t) {
+      const int i = lane + 32 * t;
+      Y[t] = i < N * C ? unpack(zbuf[i]) : dfc{{0.f, 0.f}, {0.f, 0.f}};
+    }
+    if (lane < C) ynext[lane] = zbuf[(N - 1) * C + lane];
+    __syncwarp();
+    for (int k = N - 1; k >= 0; --k) {
+      if (lane < C) {
+        const float2 iv = invd[k];
+        const float4 x = pack(scale(unpack(ynext[lane]), df{iv.x, iv.y}));
+        zc[lane] = x;
+        zbuf[k * C + lane] = x;
+      }
+      __syncwarp();
+      if (k > 0) {
+        const int t1 = (k * C - 1) >> 5;  // the last slot holding an entry of a row r < k
+#pragma unroll
+        for (int t = 0; t < SY; ++t) {
+          if (t > t1) break;
+          const int r = yk[t] >> 8, c = yk[t] & 255;
+          // x_r -= conj(L_kr) x_k, L_kr = entry (k, r) of column r; the entries of rows
+          // r >= k are final (in zbuf) and their registers are no longer read
+          const int li = r < k ? col_start(r, N) + (k - r) : 0;
+          sub_conj_mul(Y[t], unpack(Ls[li]), unpack(zc[c]));
+          if (r == k - 1) ynext[c] = pack(Y[t]);
+        }
+      }
+      __syncwarp();
+    }
 #pragma unroll
     for (int h = 0; h < R; ++h) {
       const int r = lane + 32 * h;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         if (c < C && r < N) y[h][c] = unpack(zbuf[r * C + c]);
-    }
-    // back substitution L* x = z
-    for (int k = N - 1; k >= 0; --k) {
-      const float2 iv = invd[k];
-      const df inv = {iv.x, iv.y};
-      const int owner = k & 31, hk = k >> 5;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (c < C) {
-          float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-          for (int h = 0; h < R; ++h)
-            if (h == hk) mine = pack(y[h][c]);
-          const dfc xk = scale(unpack(shfl4(mine, owner)), inv);
-#pragma unroll
-          for (int h = 0; h < R; ++h) {
-            const int r = lane + 32 * h;
-            // x_r -= conj(L_kr) x_k for r < k; L_kr is entry (k, r) of column r
-            if (r < k) sub_conj_mul(y[h][c], unpack(Ls[col_start(r, N) + (k - r)]), xk);
-            else if (r == k) y[h][c] = xk;
-          }
-        }
-      }
     }
     const long long plane = (long long)p.H * (M + 1);
     const long long off = (long long)ky * (M + 1) + kx;
