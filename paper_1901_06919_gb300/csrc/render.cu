@@ -80,40 +80,83 @@ constexpr int kRenderWarps = 8;
 constexpr int kTileMaxLC = 256;  // N * C of an FDL staged in shared memory
 
 // sum over layers k = k0, k0 + kstep, ... < r.N of the Eq. BsFourier terms of request r at
-// this lane's frequency; layer values from the shared tile when given, else from global
-// shb: this request's per-layer shifts P_k (the relaxed model) or null: u0 d_k
-__device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
-                                             float wx, float wabs, long long plane, long long off, bool valid,
-                                             const float2* tile, const float* dsh, int lane, float2 acc[4],
-                                             const float2* __restrict__ shb, const Freq& fq) {
+// this lane's frequency; layer values from the shared tile (TILE) or from global memory;
+// SHIFTS: the request's per-layer shifts P_k in shb (the relaxed model), else u0 d_k.
+// AP: 0 no aperture factor (pinhole, or a disc of radius 0), 1 disc, 2 drawn (table),
+// 3 square or points.
+template <bool TILE, bool SHIFTS, int AP>
+__device__ __forceinline__ void render_terms_t(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
+                                               float wx, float wabs, long long plane, long long off, bool valid,
+                                               const float2* tile, const float* dsh, int lane, float2 acc[4],
+                                               const float2* __restrict__ shb, const Freq& fq) {
   const float2* x = reinterpret_cast<const float2*>(r.layers);
   const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
   for (int k = k0; k < r.N; k += kstep) {
-    const float dk = tile ? dsh[k] : __ldg(r.d + k);
-    float2 sh;
+    const float dk = TILE ? dsh[k] : __ldg(r.d + k);
     float ph;
-    if (shb != nullptr) {
+    if constexpr (SHIFTS) {
       const float2 pk = __ldg(shb + k);
       ph = phase_cycles(pk.x, pk.y, fq, 1.f);
     } else {
       ph = phase_from_theta(theta, dk);
     }
-    sincospif(2.f * ph, &sh.y, &sh.x);
-    const float sd = r.s - dk;
-    float2 coef = sh;
-    if (r.aperture == FDL_AP_DISC && r.radius != 0.f) {
-      const float z = zscale * fabsf(sd);
-      coef = cscale(sh, z < 1e-3f ? 1.f - 0.125f * z * z : 2.f * j1f(z) / z);
-    } else if (r.aperture == FDL_AP_TABLE) {
-      coef = cmul(sh, aperture_table_hat(reinterpret_cast<const float2*>(r.pts), r.npts, r.radius, sd * wy, sd * wx));
-    } else if (r.aperture != FDL_AP_PINHOLE && r.aperture != FDL_AP_DISC) {
-      coef = cmul(sh, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
+    // |2 pi ph| <= pi: the hardware sine and cosine (absolute error about 2^-21 there)
+    // keep |coef| within 1e-6 of exact, far below the FP32 sum over layers it enters
+    float2 coef;
+    __sincosf(6.28318531f * ph, &coef.y, &coef.x);
+    if constexpr (AP != 0) {
+      const float sd = r.s - dk;
+      if constexpr (AP == 1) {
+        const float z = zscale * fabsf(sd);
+        coef = cscale(coef, z < 1e-3f ? 1.f - 0.125f * z * z : 2.f * j1f(z) / z);
+      } else if constexpr (AP == 2) {
+        coef = cmul(coef, aperture_table_hat(reinterpret_cast<const float2*>(r.pts), r.npts, r.radius, sd * wy, sd * wx));
+      } else {
+        coef = cmul(coef, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
+      }
     }
     if (valid) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        if (c < C) cfma(acc[c], coef, tile ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off));
+        if (c < C) cfma(acc[c], coef, TILE ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off));
     }
+  }
+}
+
+template <bool TILE, bool SHIFTS>
+__device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
+                                                float wx, float wabs, long long plane, long long off, bool valid,
+                                                const float2* tile, const float* dsh, int lane, float2 acc[4],
+                                                const float2* __restrict__ shb, const Freq& fq) {
+  const int ap = (r.aperture == FDL_AP_PINHOLE || (r.aperture == FDL_AP_DISC && r.radius == 0.f)) ? 0
+                 : r.aperture == FDL_AP_DISC                                                  ? 1
+                 : r.aperture == FDL_AP_TABLE                                                 ? 2
+                                                                                              : 3;
+#define FDL_TERMS(A) \
+  render_terms_t<TILE, SHIFTS, A>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq)
+  if (ap == 0) FDL_TERMS(0);
+  else if (ap == 1) FDL_TERMS(1);
+  else if (ap == 2) FDL_TERMS(2);
+  else FDL_TERMS(3);
+#undef FDL_TERMS
+}
+
+// the request's terms with the loop specialised for where the layers live, the shift model
+// and the aperture kind (all uniform over the request)
+__device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
+                                             float wx, float wabs, long long plane, long long off, bool valid,
+                                             const float2* tile, const float* dsh, int lane, float2 acc[4],
+                                             const float2* __restrict__ shb, const Freq& fq) {
+  if (tile != nullptr) {
+    if (shb != nullptr)
+      render_terms_ap<true, true>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
+    else
+      render_terms_ap<true, false>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
+  } else {
+    if (shb != nullptr)
+      render_terms_ap<false, true>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
+    else
+      render_terms_ap<false, false>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
   }
 }
 
