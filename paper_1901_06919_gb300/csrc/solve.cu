@@ -62,8 +62,6 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
     float2 y[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) y[c] = make_float2(0.f, 0.f);
-    bool finite = true;
-
     for (int j0 = 0; j0 < K; j0 += kViewChunk) {
       const int nv = min(kViewChunk, K - j0);
       __syncthreads();
@@ -95,15 +93,19 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           if (c < C) {
-            const float2 bv = bstage[(jj * C + c) * kTileBins + warp];
-            finite = finite && isfinite(bv.x) && isfinite(bv.y);
-            cfmac(y[c], a, bv);
+            cfmac(y[c], a, bstage[(jj * C + c) * kTileBins + warp]);
           }
         }
         __syncwarp();
       }
     }
 
+    // an input that is not finite reaches every right-hand side (|A_jk| = 1): lane 0's
+    // row is checked
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < C) finite = finite && isfinite(y[c].x) && isfinite(y[c].y);
     // regulariser lambda Gamma*Gamma
     {
       const float w2 = wx * wx + wy * wy;
@@ -149,8 +151,9 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       }
     }
 
-    // Cholesky G = L L*, row i in lane i
+    // Cholesky G = L L*, row i in lane i; lane k keeps 1 / L_kk
     bool ok = true;
+    float dinv = 1.f;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) {
       if (k < N) {
@@ -159,7 +162,10 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
         const float lkk = sqrtf(fmaxf(piv, 1e-30f));
         const float inv = 1.f / lkk;
         if (lane > k) G[k] = cscale(G[k], inv);
-        else if (lane == k) G[k] = make_float2(lkk, 0.f);
+        else if (lane == k) {
+          G[k] = make_float2(lkk, 0.f);
+          dinv = inv;
+        }
         if (lane < NMAX) myA[lane] = G[k];  // column k: L_lk in lane l
         __syncwarp();
 #pragma unroll
@@ -174,7 +180,6 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
     for (int l = 0; l < NMAX; ++l)
       if (lane < NMAX) myL[lane * (NMAX + 1) + l] = (l <= lane) ? G[l] : make_float2(0.f, 0.f);
     __syncwarp();
-    const float lii = lane < N ? myL[lane * (NMAX + 1) + lane].x : 1.f;
 
     // solves: C right-hand sides plus the inverse-iteration vector v
     float2 v = make_float2(0.f, 0.f);
@@ -183,13 +188,16 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       sincospif(2.f * 0.6180339887f * (float)(lane * lane), &s, &c);
       v = make_float2(c * rsqrtf((float)N), s * rsqrtf((float)N));
     }
+    // a factorisation that broke down is not solved (the frequency is re-solved or zeroed);
+    // without the estimate only the right-hand sides are
     float vnorm = 0.f;
-    for (int it = 0; it < 3; ++it) {
+    const int iters = ok ? (estimate ? 3 : 1) : 0;
+    for (int it = 0; it < iters; ++it) {
       // forward: L z = rhs
       for (int k = 0; k < N; ++k) {
-        const float lkk = __shfl_sync(0xffffffffu, lii, k);
+        const float ikk = __shfl_sync(0xffffffffu, dinv, k);
         const float2 lik = myL[(lane < NMAX ? lane : 0) * (NMAX + 1) + k];
-        const float2 vk = cscale(make_float2(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k)), 1.f / lkk);
+        const float2 vk = cscale(make_float2(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k)), ikk);
         if (lane > k) cfms_c(v, lik, cconj(vk));
         else if (lane == k) v = vk;
         if (it == 0) {
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
           for (int c = 0; c < 4; ++c) {
             if (c < C) {
               const float2 yk = cscale(make_float2(__shfl_sync(0xffffffffu, y[c].x, k),
-                                                   __shfl_sync(0xffffffffu, y[c].y, k)), 1.f / lkk);
+                                                   __shfl_sync(0xffffffffu, y[c].y, k)), ikk);
               if (lane > k) cfms_c(y[c], lik, cconj(yk));
               else if (lane == k) y[c] = yk;
             }
@@ -206,9 +214,9 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       }
       // backward: L* x = z
       for (int k = N - 1; k >= 0; --k) {
-        const float lkk = __shfl_sync(0xffffffffu, lii, k);
+        const float ikk = __shfl_sync(0xffffffffu, dinv, k);
         const float2 lki = myL[k * (NMAX + 1) + (lane < NMAX ? lane : 0)];  // L_ki
-        const float2 vk = cscale(make_float2(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k)), 1.f / lkk);
+        const float2 vk = cscale(make_float2(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k)), ikk);
         if (lane < k) cfms_c(v, cconj(lki), cconj(vk));  // v_i -= conj(L_ki) x_k
         else if (lane == k) v = vk;
         if (it == 0) {
@@ -216,7 +224,7 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
           for (int c = 0; c < 4; ++c) {
             if (c < C) {
               const float2 yk = cscale(make_float2(__shfl_sync(0xffffffffu, y[c].x, k),
-                                                   __shfl_sync(0xffffffffu, y[c].y, k)), 1.f / lkk);
+                                                   __shfl_sync(0xffffffffu, y[c].y, k)), ikk);
               if (lane < k) cfms_c(y[c], cconj(lki), cconj(yk));
               else if (lane == k) y[c] = yk;
             }
@@ -252,7 +260,8 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       const bool trusted = ok && finite && isfinite(kappa) && kappa <= p.kappa_max && isfinite(n2);
       if (lane == 0 && qown) {
         p.err[q] = trusted ? kappa * sqrtf(n2) : INFINITY;
-        p.xn2[q] = isfinite(n2) ? n2 : 0.f;
+        // |x|^2 for the budget's |X|: 0 where the factorisation broke down (no solution)
+        p.xn2[q] = (ok && isfinite(n2)) ? n2 : 0.f;
       }
     }
     if (lane == 0 && qown) {
