@@ -24,3 +24,4 @@ from .fdl import (  # noqa: F401
     rfft2,
     workspace,
 )
+from .pipeline import FitRenderPipeline  # noqa: F401,E402
