@@ -47,8 +47,10 @@ constexpr int df_min_blocks(int nmax) { return nmax <= 16 ? 4 : (nmax <= 32 ? 3 
 
 // float4 words of shared memory per warp: A_j / next pivot column and the current column
 // (NMAX + 1 each), the packed factor, [NMAX][4] right-hand sides, 2 x 4 pivot-row values,
-// NMAX double-float reciprocals
-__host__ __device__ constexpr int df_warp_f4(int nmax) { return 2 * (nmax + 1) + nmax * (nmax + 1) / 2 + 4 * nmax + 8 + (nmax + 1) / 2; }
+// NMAX double-float reciprocals, 3 x 32 view-only values of a chunk of views (moment form)
+__host__ __device__ constexpr int df_warp_f4(int nmax) {
+  return 2 * (nmax + 1) + nmax * (nmax + 1) / 2 + 4 * nmax + 8 + (nmax + 1) / 2 + 96;
+}
 
 // entry (r, l), l <= r, numbered column-major: column l starts at l*N - l(l-1)/2
 __device__ __forceinline__ int col_start(int l, int N) { return l * N - (l * (l - 1)) / 2; }
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
   float4* ynext = zbuf + 4 * NMAX;               // [C] right-hand sides of the next pivot row
   float4* zc = ynext + 4;                        // [C] z of the current pivot row
   float2* invd = reinterpret_cast<float2*>(zc + 4);  // 1 / L_kk as df
+  float4* thb = reinterpret_cast<float4*>(invd) + (NMAX + 1) / 2;  // [32][3] view-only values
 
   // coordinates (r, l) of this lane's slots, packed as r * 256 + l.  An unused slot
   // (entry number >= E) gets (N, N): it reads Arow[N] / col[N], which lie inside this
@@ -319,77 +322,116 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
       __syncwarp();
     }
 
-    for (int j = 0; j < K; ++j) {
-      const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
-      const ThetaX th = theta_r(uj.x, uj.y, fq, Rdf{});
-      float2 bj[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        bj[c] = c < C ? (stage ? bst[j * C + c] : *p.b.at((long long)j * C + c, ky, kx, M)) : make_float2(0.f, 0.f);
-      dfc aR[R];  // A_jr of this lane's rows (moment form)
-#pragma unroll
-      for (int h = 0; h < R; ++h) {
-        const int r = lane + 32 * h;
-        aR[h] = {{0.f, 0.f}, {0.f, 0.f}};
-        if (r < N) {
-          const cx<Rdf> a = cexp2pi(phase_r(th, dr[h]), tab);
-          aR[h] = {a.re.v, a.im.v};
-          // A - 1: the subtraction of the high word is exact (TwoSum)
-          const df t = two_sum(a.re.v.hi, -1.f);
-          const df am = two_sum(t.hi, __fadd_rn(t.lo, a.re.v.lo));
-          const float4 av = make_float4(am.hi, a.im.v.hi, am.lo, a.im.v.lo);
-          if constexpr (!MOM) {
-            Arow[r] = av;
-            const df s1 = two_sum(Ssum[h].re.hi, am.hi);
-            Ssum[h].re = two_sum(s1.hi, __fadd_rn(__fadd_rn(Ssum[h].re.lo, s1.lo), am.lo));
-            const df s2 = two_sum(Ssum[h].im.hi, a.im.v.hi);
-            Ssum[h].im = two_sum(s2.hi, __fadd_rn(__fadd_rn(Ssum[h].im.lo, s2.lo), a.im.v.lo));
-          }
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (c < C) rhs_acc(y[h][c], av, bj[c]);
-        }
-      }
+    for (int j0 = 0; j0 < K; j0 += 32) {
       if constexpr (MOM) {
-        // w_jm = A_jm conj(A_j0) for this lane's m (A_j0 from lane 0) and the moments of w - 1
-        const df theta = df_add(two_sum(th.p1, th.p2), df_from(__fadd_rn(__fadd_rn(th.e1, th.e2), th.g)));
-        const float th2 = theta.hi * theta.hi, th3 = th2 * theta.hi;
-        acc_df(T1, theta);
-        T2 += th2;
-        T3 += th3;
-        const dfc a0 = unpack(shfl4(pack(aR[0]), 0));
+        // what depends on the view only (theta = u_j . w in exact pieces and as a double-float,
+        // theta^2, theta^3 and their sums), once per view: one view per lane for a chunk of 32
+        const int jl = j0 + lane;
+        if (jl < K) {
+          const float2 ul = __ldg(reinterpret_cast<const float2*>(p.u) + jl);
+          const ThetaX t = theta_r(ul.x, ul.y, fq, Rdf{});
+          const df theta = df_add(two_sum(t.p1, t.p2), df_from(__fadd_rn(__fadd_rn(t.e1, t.e2), t.g)));
+          const float th2 = theta.hi * theta.hi, th3 = th2 * theta.hi;
+          thb[3 * lane] = make_float4(t.p1, t.e1, t.p2, t.e2);
+          thb[3 * lane + 1] = make_float4(t.g, theta.hi, theta.lo, th2);
+          thb[3 * lane + 2] = make_float4(th3, 0.f, 0.f, 0.f);
+          acc_df(T1, theta);
+          T2 += th2;
+          T3 += th3;
+        }
+        __syncwarp();
+      }
+      const int jn = min(32, K - j0);
+      for (int jj = 0; jj < jn; ++jj) {
+        const int j = j0 + jj;
+        ThetaX th;
+        df theta = {0.f, 0.f};
+        float th2 = 0.f, th3 = 0.f;
+        if constexpr (MOM) {
+          const float4 q0 = thb[3 * jj], q1 = thb[3 * jj + 1];
+          th = {q0.x, q0.y, q0.z, q0.w, q1.x};
+          theta = {q1.y, q1.z};
+          th2 = q1.w;
+          th3 = thb[3 * jj + 2].x;
+        } else {
+          const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
+          th = theta_r(uj.x, uj.y, fq, Rdf{});
+        }
+        float2 bj[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          bj[c] = c < C ? (stage ? bst[j * C + c] : *p.b.at((long long)j * C + c, ky, kx, M)) : make_float2(0.f, 0.f);
+        dfc aR[R];  // A_jr of this lane's rows (moment form)
 #pragma unroll
         for (int h = 0; h < R; ++h) {
-          if (lane + 32 * h < N) {
-            const dfc& am = aR[h];
-            const df wr = sadd_df(df_mul(am.re, a0.re), df_mul(am.im, a0.im));
-            const df wi = sadd_df(df_mul(am.im, a0.re), df_neg(df_mul(am.re, a0.im)));
-            // w - 1 (exact subtraction of the high word)
-            const df t = two_sum(wr.hi, -1.f);
-            const df wm1r = two_sum(t.hi, __fadd_rn(t.lo, wr.lo));
-            acc_df(M0[h].re, wm1r);
-            acc_df(M0[h].im, wi);
-            acc_df(M1[h].re, df_mul(theta, wm1r));
-            acc_df(M1[h].im, df_mul(theta, wi));
-            M2[h].x = fmaf(th2, wm1r.hi, M2[h].x);
-            M2[h].y = fmaf(th2, wi.hi, M2[h].y);
-            M3[h].x = fmaf(th3, wm1r.hi, M3[h].x);
-            M3[h].y = fmaf(th3, wi.hi, M3[h].y);
+          const int r = lane + 32 * h;
+          aR[h] = {{0.f, 0.f}, {0.f, 0.f}};
+          if (r < N) {
+            const cx<Rdf> a = cexp2pi(phase_r(th, dr[h]), tab);
+            aR[h] = {a.re.v, a.im.v};
+            // A - 1: the subtraction of the high word is exact (TwoSum)
+            const df t = two_sum(a.re.v.hi, -1.f);
+            const df am = two_sum(t.hi, __fadd_rn(t.lo, a.re.v.lo));
+            const float4 av = make_float4(am.hi, a.im.v.hi, am.lo, a.im.v.lo);
+            if constexpr (!MOM) {
+              Arow[r] = av;
+              const df s1 = two_sum(Ssum[h].re.hi, am.hi);
+              Ssum[h].re = two_sum(s1.hi, __fadd_rn(__fadd_rn(Ssum[h].re.lo, s1.lo), am.lo));
+              const df s2 = two_sum(Ssum[h].im.hi, a.im.v.hi);
+              Ssum[h].im = two_sum(s2.hi, __fadd_rn(__fadd_rn(Ssum[h].im.lo, s2.lo), a.im.v.lo));
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (c < C) rhs_acc(y[h][c], av, bj[c]);
           }
         }
-        continue;
-      }
-      __syncwarp();
-      // every slot, without a branch, so that the independent slot updates interleave;
-      // diagonal slots are overwritten below (the sum of |A_jk|^2 is exactly K)
+        if constexpr (MOM) {
+          // w_jm = A_jm conj(A_j0) for this lane's m (A_j0 from lane 0) and the moments of w - 1
+          const dfc a0 = unpack(shfl4(pack(aR[0]), 0));
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        gram_acc(G[s], Arow[SR(s)], Arow[SL(s)]);
-        // keep |lo| within an ulp of |hi| so that the low word's own rounding stays at 2^-48
-        G[s].re = fast_two_sum(G[s].re.hi, G[s].re.lo);
-        G[s].im = fast_two_sum(G[s].im.hi, G[s].im.lo);
+          for (int h = 0; h < R; ++h) {
+            if (lane + 32 * h < N) {
+              const dfc& am = aR[h];
+              const df wr = sadd_df(df_mul(am.re, a0.re), df_mul(am.im, a0.im));
+              const df wi = sadd_df(df_mul(am.im, a0.re), df_neg(df_mul(am.re, a0.im)));
+              // w - 1 (exact subtraction of the high word)
+              const df t = two_sum(wr.hi, -1.f);
+              const df wm1r = two_sum(t.hi, __fadd_rn(t.lo, wr.lo));
+              acc_df(M0[h].re, wm1r);
+              acc_df(M0[h].im, wi);
+              acc_df(M1[h].re, df_mul(theta, wm1r));
+              acc_df(M1[h].im, df_mul(theta, wi));
+              M2[h].x = fmaf(th2, wm1r.hi, M2[h].x);
+              M2[h].y = fmaf(th2, wi.hi, M2[h].y);
+              M3[h].x = fmaf(th3, wm1r.hi, M3[h].x);
+              M3[h].y = fmaf(th3, wi.hi, M3[h].y);
+            }
+          }
+          continue;
+        }
+        __syncwarp();
+        // every slot, without a branch, so that the independent slot updates interleave;
+        // diagonal slots are overwritten below (the sum of |A_jk|^2 is exactly K)
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          gram_acc(G[s], Arow[SR(s)], Arow[SL(s)]);
+          // keep |lo| within an ulp of |hi| so that the low word's own rounding stays at 2^-48
+          G[s].re = fast_two_sum(G[s].re.hi, G[s].re.lo);
+          G[s].im = fast_two_sum(G[s].im.hi, G[s].im.lo);
+        }
+        __syncwarp();
       }
-      __syncwarp();
+      if constexpr (MOM) __syncwarp();  // the next chunk rewrites thb
+    }
+    if constexpr (MOM) {
+      // the sums of theta^p over the views, from the lanes' partial sums
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const df t = {__shfl_xor_sync(0xffffffffu, T1.hi, o), __shfl_xor_sync(0xffffffffu, T1.lo, o)};
+        T1 = df_add(T1, t);
+        T2 += __shfl_xor_sync(0xffffffffu, T2, o);
+        T3 += __shfl_xor_sync(0xffffffffu, T3, o);
+      }
     }
     // Assemble A*A and A*b from the sums over (A - 1).  With a = 1 + a~,
     //   conj(a_r) a_l = 1 + conj(a~_r) + a~_l + conj(a~_r) a~_l,
