@@ -68,6 +68,30 @@ __device__ __forceinline__ float2 aperture_table_hat(const float2* __restrict__ 
   return make_float2(w00 * a.x + w01 * b.x + w10 * c.x + w11 * e.x, w00 * a.y + w01 * b.y + w10 * c.y + w11 * e.y);
 }
 
+// psi_hat of a disc, 2 J1(z) / z for z >= 0, from the rational approximations of Abramowitz
+// and Stegun, Handbook of Mathematical Functions, 9.4.4 (z <= 3: J1(z) / z as a polynomial in
+// (z/3)^2, error below 1.3e-8) and 9.4.6 (z > 3: J1 = z^-1/2 f1 cos(theta1), f1 and theta1
+// polynomials in 3/z, errors below 4e-8 and 9e-8); theta1 is reduced to [-pi, pi] with a
+// two-part 2 pi before the SFU cosine.
+__device__ __forceinline__ float disc_hat(float z) {
+  if (z <= 3.f) {
+    const float t = z * z * (1.f / 9.f);
+    return 2.f * (0.5f +
+                  t * (-0.56249985f +
+                       t * (0.21093573f + t * (-0.03954289f + t * (0.00443319f + t * (-0.00031761f + t * 0.00001109f))))));
+  }
+  const float y = __fdividef(3.f, z);
+  const float f1 =
+      0.79788456f +
+      y * (0.00000156f + y * (0.01659667f + y * (0.00017105f + y * (-0.00249511f + y * (0.00113653f + y * -0.00020033f)))));
+  float th = z - 2.35619449f +
+             y * (0.12499612f + y * (0.00005650f + y * (-0.00637879f + y * (0.00074348f + y * (0.00079824f + y * -0.00029166f)))));
+  const float n = rintf(th * 0.15915494f);
+  th = fmaf(-n, 6.28125f, th);
+  th = fmaf(-n, 1.9353071795864769e-3f, th);
+  return 2.f * f1 * __cosf(th) * rsqrtf(z) * (y * (1.f / 3.f));  // 2 J1(z) / z = 2 f1 cos(theta1) z^-3/2
+}
+
 // Phase of exp(+2 pi i d (u0 . w)) in cycles, reduced to [-1/2, 1/2], from
 // theta = u0 . w kept as a double-float (computed once per request and bin).
 __device__ __forceinline__ float phase_from_theta(df theta, float d) {
@@ -107,8 +131,7 @@ __device__ __forceinline__ void render_terms_t(const fdl_request& r, int k0, int
     if constexpr (AP != 0) {
       const float sd = r.s - dk;
       if constexpr (AP == 1) {
-        const float z = zscale * fabsf(sd);
-        coef = cscale(coef, z < 1e-3f ? 1.f - 0.125f * z * z : 2.f * j1f(z) / z);
+        coef = cscale(coef, disc_hat(zscale * fabsf(sd)));
       } else if constexpr (AP == 2) {
         coef = cmul(coef, aperture_table_hat(reinterpret_cast<const float2*>(r.pts), r.npts, r.radius, sd * wy, sd * wx));
       } else {
