@@ -847,10 +847,10 @@ def moment_form_applies(u, d):
 SURVEY_FLOPS_PER_FREQUENCY = 145_000
 
 # DRAM bytes (read + write) per frequency of k_solve_df<30, 15, moment form>, from one ncu capture
-# of the mixed fit's double-float launch on this workload (74,398 listed frequencies: 156.98 MB
-# read, 36.43 MB written).  The algorithmic bytes are the K x C spectrum values read and the
+# of the mixed fit's double-float launch on this workload (74,398 listed frequencies: 156.61 MB
+# read, 36.21 MB written).  The algorithmic bytes are the K x C spectrum values read and the
 # N x C layer values written, 8 bytes each: 2,664 per frequency.
-DF_DRAM_BYTES_PER_FREQUENCY = (156.984576e6 + 36.430592e6) / 74_398
+DF_DRAM_BYTES_PER_FREQUENCY = (156.608512e6 + 36.205568e6) / 74_398
 
 
 def roofline_entry(legs, clk, moment):
