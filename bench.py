@@ -844,7 +844,7 @@ def moment_form_applies(u, d):
 
 # Algorithmic flops per frequency of an FP32 solve with a Toeplitz Gram (9x9 views, N = 30, RGB):
 # Gram 14.6k, A 14.6k, right-hand side 58.3k, Cholesky 36k, solves 21.6k.
-SURVEY_FLOPS_PER_FREQUENCY = 145_000
+FP32_METHOD_FLOPS_PER_FREQUENCY = 145_000
 
 # DRAM bytes (read + write) per frequency of k_solve_df<30, 15, moment form>, from one ncu capture
 # of the mixed fit's double-float launch on this workload (74,398 listed frequencies: 156.61 MB
@@ -869,8 +869,8 @@ def roofline_entry(legs, clk, moment):
             "algorithmic_bytes": ((2 * GRID + 1) ** 2 + N) * C * 8 * q_half(),
             "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock sampled in the run)",
             "work_per_frequency_fp32_ops": per_q,
-            "fp32_method_flops_per_frequency": SURVEY_FLOPS_PER_FREQUENCY,
-            "fp32_method_tflops": SURVEY_FLOPS_PER_FREQUENCY * q_half() / (ms / 1e3) / 1e12}
+            "fp32_method_flops_per_frequency": FP32_METHOD_FLOPS_PER_FREQUENCY,
+            "fp32_method_tflops": FP32_METHOD_FLOPS_PER_FREQUENCY * q_half() / (ms / 1e3) / 1e12}
 
 
 if __name__ == "__main__":

@@ -60,7 +60,7 @@ extern "C" {
 #define FDL_ENOMEM 2   /* workspace smaller than the *_workspace_size()    */
 #define FDL_ECUDA 3    /* a kernel launch or CUDA runtime call failed       */
 #define FDL_ETIMEOUT 4 /* a bounded wait ran out                            */
-#define FDL_ENOTSUP 5  /* valid request this build does not support         */
+#define FDL_ENOTSUP 5  /* valid request the library does not support        */
 
 /* ---- regularisers, Sec. V-C -------------------------------------------- */
 #define FDL_REG_VIEW2 0  /* Gamma*Gamma = diag(|w|^4 d_k^4 + eps), Eq. 2ndOrderView */

@@ -258,7 +258,7 @@ FDL_API const char* fdl_strerror(int status) {
     case FDL_ETIMEOUT:
       return "bounded wait timed out";
     case FDL_ENOTSUP:
-      return "not supported by this build";
+      return "not supported by the library";
     default:
       return "unknown status";
   }
