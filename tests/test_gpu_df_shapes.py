@@ -2,8 +2,8 @@
 and channel counts that do not fill its register slots: N below the compiled size (unused
 slots of the factorisation), N across the one- and two-rows-per-lane boundary (N > 32), and
 1, 2 or 4 channels (partly used right-hand-side slots), in the moment form (disparities on a
-grid) and the direct form (irregular disparities).  Layers against the FP64 oracle within
-relative L2 1e-5.
+grid) and the direct form (irregular disparities); and more inputs per frequency than the
+kernel stages.  Layers against the FP64 oracle within relative L2 1e-5.
 """
 
 import numpy as np
@@ -40,3 +40,17 @@ def test_df_layer_and_channel_counts(fdl, N, C, grid):
     assert _rel(got, ref) < TOL
     t = ws.tier_counts()
     assert t["df"] + t["fp64"] == 24 * 13 and t["breakdown"] == 0
+
+
+@pytest.mark.parametrize("g,N,C", [(2, 6, 4), (3, 7, 3)])
+def test_df_inputs_read_per_view(fdl, g, N, C):
+    """More spectrum values per frequency (K x C) than the kernel's staging area holds for
+    this layer count (N <= 8: 72 values): the view loop reads them from global memory."""
+    u = view_grid(g)
+    assert len(u) * C > 72
+    d = np.linspace(-2.0, 2.0, N).astype(np.float32)
+    views, _ = occluding_planes(N + 5 * C, 24, 24, C, u)
+    ref = O.fit(views, u, d.astype(np.float64), lam=1e-1, eps=1e-4)
+    x, _ = fdl.fit(torch.from_numpy(views).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(d).cuda(), 1e-1,
+                   precision="df")
+    assert _rel(x.cpu().numpy(), ref) < TOL
