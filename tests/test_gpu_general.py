@@ -96,6 +96,19 @@ def test_render_with_shifts(fdl, H, W):
     assert torch.max(torch.abs(a - b_)).item() < 1e-5
 
 
+def test_render_with_shifts_many_requests(fdl):
+    """Nine requests on one FDL: the CTA stages the layers in shared memory once (the batched
+    path) while every request brings its own per-layer shifts."""
+    H, W = 32, 40
+    X = random_layer_spectra(12, 6, 3, H, W)
+    rng = np.random.default_rng(12)
+    P = rng.uniform(-2.5, 2.5, (9, 6, 2)).astype(np.float32)
+    imgs = fdl.render_shifts(_dev(X), _dev(P), W=W).cpu().numpy()
+    for b in range(9):
+        ref = O.render_shifts(X.astype(np.complex128), P[b].astype(np.float64), W=W)
+        assert np.max(np.abs(imgs[b] - ref)) < 1e-4
+
+
 @pytest.mark.parametrize("reg,precision", [("layer2", "df"), ("l2", "f64")])
 def test_shift_gradient_matches_oracle(fdl, reg, precision):
     rng = np.random.default_rng(3)
