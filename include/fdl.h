@@ -62,6 +62,18 @@ extern "C" {
 #define FDL_ETIMEOUT 4 /* a bounded wait ran out                            */
 #define FDL_ENOTSUP 5  /* valid request the library does not support        */
 
+/* ---- device status word ------------------------------------------------
+ * Conditions found on the device cannot be returned by the enqueuing call:
+ * the kernels OR these bits into a status word at the start of the call's
+ * workspace (cleared by each call), read by fdl_sync_status. */
+#define FDL_ST_NONFINITE 1   /* fit: a frequency had non-finite input; its layer
+                                values are not finite                            */
+#define FDL_ST_BREAKDOWN 2   /* fit: the last factorisation of a frequency broke
+                                down (a pivot not positive); its layers are zero */
+#define FDL_ST_BAD_REQUEST 4 /* render: a request failed the device-side checks
+                                (sizes, N, pointers, aperture, parameters) and
+                                was skipped; its output is left untouched        */
+
 /* ---- regularisers, Sec. V-C -------------------------------------------- */
 #define FDL_REG_VIEW2 0  /* Gamma*Gamma = diag(|w|^4 d_k^4 + eps), Eq. 2ndOrderView */
 #define FDL_REG_LAYER2 1 /* Gamma = tridiag(1,-2,1), Eq. 2ndOrderLayer              */
@@ -72,7 +84,10 @@ extern "C" {
                             f32_error_budget; double-float (FP32 pairs,
                             ~2^-48) elsewhere, except the frequencies that
                             native FP64 must take to meet df_error_budget     */
-#define FDL_PREC_DF 1    /* double-float at every frequency                   */
+#define FDL_PREC_DF 1    /* double-float at every frequency, certified like the
+                            mixed path: the frequencies that native FP64 must
+                            take to meet df_error_budget are re-solved in FP64
+                            (N <= 48; beyond, double-float only)              */
 #define FDL_PREC_F64 2   /* native FP64 at every frequency                    */
 #define FDL_PREC_F32 3   /* FP32 at every frequency, no certification         */
 
@@ -94,7 +109,7 @@ typedef struct fdl_fit_opts {
                        A*A + lambda Gamma*Gamma whose FP32 solution may be kept at
                        all; above it the estimate itself is not trusted
                        (<= 0 selects the default, 1e6)                             */
-  double df_error_budget; /* FDL_PREC_MIXED: estimated relative L2 error that the
+  double df_error_budget; /* FDL_PREC_MIXED, FDL_PREC_DF: estimated relative L2 error that the
                              double-float frequencies may leave in the layers; the
                              frequencies with the largest estimated errors (condition
                              estimate x solution norm), and any whose double-float
@@ -110,7 +125,10 @@ typedef struct fdl_fit_opts {
 } fdl_fit_opts;
 
 /* One image to render (Eq. BsFourier): the FDL it reads, the viewpoint u0,
- * the focus disparity s and the aperture. */
+ * the focus disparity s, the aperture and the image size.  The descriptors
+ * live in device memory, so the host cannot check them: the kernels do
+ * (request_ok in the library) and skip a request that fails, setting
+ * FDL_ST_BAD_REQUEST. */
 typedef struct fdl_request {
   const float* layers; /* device complex64 [N][C][H][W/2+1]                     */
   const float* d;      /* device float32 [N]                                    */
@@ -125,7 +143,8 @@ typedef struct fdl_request {
   float radius;        /* disc radius / square half side, in units of u (the
                           aperture-size factor f of Sec. VI-A); FDL_AP_TABLE:
                           the raster pitch h, in units of u                     */
-  int pad_;            /* keeps the struct a multiple of 8 bytes; set to 0      */
+  int H, W, C;         /* image size of the FDL and of `out`                    */
+  int pad_[2];         /* keeps the struct 80 bytes; set to 0                   */
 } fdl_request;
 
 FDL_API const char* fdl_strerror(int status);
@@ -164,10 +183,10 @@ FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W,
                             void* stream);
 
 /* fdl_fit_spectra without a workspace, for callers that may not allocate device
- * memory: code running while a stream is being captured into a CUDA graph,
- * real-time loops that cannot afford cudaMalloc's implicit synchronisation,
- * and hosts (plugins, renderers, frameworks with their own caching allocator)
- * that own the whole device-memory budget and forbid allocations by libraries.
+ * memory: real-time loops that cannot afford cudaMalloc's implicit
+ * synchronisation, and hosts (plugins, renderers, frameworks with their own
+ * caching allocator) that own the whole device-memory budget and forbid
+ * allocations by libraries.
  * The paper has no counterpart: this is an integration variant only.
  * Its scratch is a fixed array inside the library (8,455,168 bytes on every
  * GPU that loads it, held until the process exits); H * (W/2 + 1) must not
@@ -181,6 +200,14 @@ FDL_API int fdl_fit_spectra_noalloc(const float* spectra, int K, int C, int H, i
                                     const float* d, int N, const fdl_fit_opts* opts, float* layers,
                                     void* stream);
 
+/* The device status word (FDL_ST_* bits, 0 if nothing was found) of the last
+ * call that used `workspace`: fdl_fit, fdl_fit_spectra, fdl_fit_general,
+ * fdl_render, fdl_refocus or fdl_render_shifts.  status is a HOST int; this
+ * call synchronises `stream` (the call's stream).  The error convention of the
+ * boundary: FDL_E* codes for what the host can check before enqueuing,
+ * FDL_ST_* bits for what only the kernels see. */
+FDL_API int fdl_sync_status(const void* workspace, int* status, void* stream);
+
 /* After fdl_fit / fdl_fit_spectra on `stream`: counts[0] = frequencies solved
  * in FP32, counts[1] = in double-float, counts[2] = in native FP64,
  * counts[3] = frequencies whose last factorisation broke down (left as
@@ -191,17 +218,23 @@ FDL_API int fdl_fit_tier_counts(const void* workspace, int* counts, void* stream
 /* ---- rendering (Sec. VI-A, Eq. FourierView / Eq. BsFourier) ----------- */
 
 /* B sub-aperture views of one FDL at viewpoints u0 [B][2] (psi = delta):
- * out [B][C][H][W]. */
+ * out [B][C][H][W].  Power-of-two sizes up to 2048 rows take the fused
+ * render + inverse column DFT of fdl_refocus.  B <= 65535. */
 FDL_API size_t fdl_render_workspace_size(int B, int C, int H, int W);
 FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H, int W,
                        const float* u0, int B, float* out, void* workspace,
                        size_t workspace_bytes, void* stream);
 
 /* B general images, each described by a request (req: DEVICE array [B]).
- * The requests may read different FDLs, but all share H, W, C (the caller
- * groups requests by image size).  If count is not NULL it is a DEVICE int:
- * only requests [0, *count) are rendered, so that a captured CUDA graph can
- * be replayed with a varying batch.  Every N must be <= Nmax <= 64. */
+ * C, H, W, Nmax bound every request: when H and W are powers of two and
+ * H <= 2048, requests of ANY power-of-two sizes H_b <= H, W_b <= W (>= 16)
+ * and C_b <= C share the launch (mixed FDLs and image sizes); each is
+ * rendered by Eq. BsFourier straight into the inverse column DFT (the
+ * rendered spectrum is never written to memory), then the inverse row DFT
+ * writes its output.  Otherwise (sizes that are not powers of two, or
+ * H = 4096) every request must have exactly H x W x C.  If count is not NULL
+ * it is a DEVICE int: only requests [0, *count) are rendered, so that a
+ * captured CUDA graph can be replayed with a varying batch.  Nmax <= 64. */
 FDL_API size_t fdl_refocus_workspace_size(int B, int C, int H, int W);
 FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, int H,
                         int W, int Nmax, void* workspace, size_t workspace_bytes,

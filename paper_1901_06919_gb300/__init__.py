@@ -19,6 +19,7 @@ from .fdl import (  # noqa: F401
     pack_views,
     refocus,
     refocus_specs,
+    sync_status,
     render,
     render_shifts,
     rfft2,

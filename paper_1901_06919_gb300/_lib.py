@@ -12,6 +12,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfdl.so")
 
 FDL_OK, FDL_EINVAL, FDL_ENOMEM, FDL_ECUDA, FDL_ETIMEOUT, FDL_ENOTSUP = range(6)
+# bits of the device status word (fdl_sync_status)
+ST_NONFINITE, ST_BREAKDOWN, ST_BAD_REQUEST = 1, 2, 4
 REG = {"view2": 0, "layer2": 1, "l2": 2}
 PREC = {"mixed": 0, "df": 1, "f64": 2, "f32": 3}
 APERTURE = {"pinhole": 0, "disc": 1, "square": 2, "points": 3, "table": 4}
@@ -28,7 +30,8 @@ class Request(ct.Structure):
 
     _fields_ = [("layers", ct.c_void_p), ("d", ct.c_void_p), ("out", ct.c_void_p), ("pts", ct.c_void_p),
                 ("N", ct.c_int), ("npts", ct.c_int), ("aperture", ct.c_int), ("u0x", ct.c_float),
-                ("u0y", ct.c_float), ("s", ct.c_float), ("radius", ct.c_float), ("pad_", ct.c_int)]
+                ("u0y", ct.c_float), ("s", ct.c_float), ("radius", ct.c_float), ("H", ct.c_int), ("W", ct.c_int),
+                ("C", ct.c_int), ("pad_", ct.c_int * 2)]
 
 
 class FdlError(RuntimeError):
@@ -64,6 +67,7 @@ _SIGS = [
     ("fdl_fit_spectra_noalloc", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
                                            ct.c_void_p, ct.c_int, ct.POINTER(FitOpts), ct.c_void_p, ct.c_void_p]),
     ("fdl_fit_tier_counts", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.c_void_p]),
+    ("fdl_sync_status", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.c_void_p]),
     ("fdl_render_workspace_size", ct.c_size_t, [ct.c_int] * 4),
     ("fdl_render", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
                               ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p]),

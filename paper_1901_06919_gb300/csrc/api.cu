@@ -94,7 +94,7 @@ struct FitWs {
 FitWs carve_fit(void* ws, int K, int C, int H, int W, bool with_spectra) {
   Carver cv(ws);
   FitWs f;
-  f.counters = cv.take<int>(16);
+  f.counters = cv.take<int>(kHeaderInts);
   f.exp_table = cv.take<float4>(1024);
   f.fft_tables = cv.take<float4>(dft_table_elems(H, W));
   f.mom = cv.take<float2>(kMomSlots);
@@ -153,7 +153,7 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
   p.counters = f.counters;
   p.exp_table = f.exp_table;
   p.mom = f.mom;
-  cudaError_t e = cudaMemsetAsync(f.counters, 0, 16 * sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(f.counters, 0, kHeaderInts * sizeof(int), st);
   if (e != cudaSuccess) return FDL_ECUDA;
   e = launch_exp_table(f.exp_table, st);
   if (e == cudaSuccess && p.mom != nullptr) e = launch_mom_check(p, st);
@@ -187,7 +187,8 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
       e = launch_solve_f32(p, false, st);
       break;
     case FDL_PREC_DF:
-      e = solve_df(true, false);
+      // double-float at every frequency, certified by the same FP64 budget as the mixed path
+      e = solve_df(true, true);
       break;
     case FDL_PREC_F64:
       e = launch_solve_hp(p, true, true, 0, st);
@@ -204,13 +205,16 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
         if (e == cudaSuccess) e = solve_df(false, true);
       }
   }
+  if (e == cudaSuccess) e = launch_fit_status(f.counters, st);
   return cuda_status(e);
 }
 
 size_t spec_tmp_bytes(int nimg, int H, int W) { return align_up((size_t)nimg * H * (W / 2) * sizeof(float2)); }
 
+// header (counters and status word), [requests], spectra (split main part; the slots of the
+// fused path), the Nyquist plane and the DFT tables of the other paths
 size_t render_ws_bytes(int B, int C, int H, int W, bool with_reqs) {
-  size_t s = 0;
+  size_t s = align_up(kHeaderInts * sizeof(int));
   if (with_reqs) s += align_up((size_t)B * sizeof(fdl_request));
   s += align_up((size_t)B * C * H * (W / 2) * sizeof(float2));
   s += align_up((size_t)B * C * H * sizeof(float2));
@@ -222,11 +226,13 @@ size_t render_ws_bytes(int B, int C, int H, int W, bool with_reqs) {
 // order (the dense layout of other sizes starts at `main` and fits in both), `tables`
 // after them.
 cudaError_t render_inverse(float2* main, float2* nyq, float4* tables, int B, int C, int H, int W, float* out,
-                           const fdl_request* req, const int* count, cudaStream_t st) {
+                           const fdl_request* req, const int* count, cudaStream_t st, int nmax = 64,
+                           const int* gate = nullptr) {
   const float scale = 1.f / ((float)H * (float)W);
   if (pow2_shape(H, W)) {
-    cudaError_t e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, count, C, st);
-    if (e == cudaSuccess) e = launch_irfft_rows(main, out, (long long)B * C * H, H, W, scale, req, count, C, st);
+    cudaError_t e = launch_fft_cols_inv(spec_split(main, nyq, H, W), main, B * C, H, W, count, C, st, gate);
+    if (e == cudaSuccess)
+      e = launch_irfft_rows(main, out, (long long)B * C * H, H, W, scale, req, count, C, st, nmax, gate);
     return e;
   }
   const GenPlans g = gen_plans(H, W);
@@ -234,11 +240,56 @@ cudaError_t render_inverse(float2* main, float2* nyq, float4* tables, int B, int
   cudaError_t e = launch_gen_tables2(g, tables, st);
   if (e == cudaSuccess) e = launch_gen_cols(sp, sp, B * C, H, W, true, g.ph, tables, count, C, st);
   if (e == cudaSuccess)
-    e = launch_gen_rows_inv(sp, out, (long long)B * C * H, H, W, scale, req, count, C, g.pw, tables, st);
+    e = launch_gen_rows_inv(sp, out, (long long)B * C * H, H, W, scale, req, count, C, g.pw, tables, st, nmax);
   return e;
 }
 SpecView render_spec_view(float2* main, float2* nyq, int H, int W) {
   return pow2_shape(H, W) ? spec_split(main, nyq, H, W) : spec_dense(main, H, W);
+}
+
+// Workspace of a render: header, [requests], then the spectra, Nyquist plane and tables.
+struct RenderWs {
+  int* header;
+  fdl_request* req;
+  float2* main;
+  float2* nyq;
+  float4* tables;
+};
+RenderWs carve_render(void* ws, int B, int C, int H, int W, bool with_reqs) {
+  Carver cv(ws);
+  RenderWs r;
+  r.header = cv.take<int>(kHeaderInts);
+  r.req = with_reqs ? cv.take<fdl_request>(B) : nullptr;
+  r.main = cv.take<float2>((size_t)B * C * H * (W / 2));
+  r.nyq = cv.take<float2>((size_t)B * C * H);
+  r.tables = cv.take<float4>(inv_table_elems(H, W));
+  return r;
+}
+
+// Renders B requests (validated on the device against C, H, W and Nmax).
+//  * tiled: spectra of exactly H x W x C with the layer values of each tile of frequencies
+//    staged once and reused by every request of one FDL, then the separate inverse DFT
+//    passes; the only path for sizes that are not powers of two, H = 4096 and per-layer shifts;
+//  * fused: Eq. BsFourier straight into the inverse column DFT, requests of any power-of-two
+//    sizes within (C, H, W) and of different FDLs in one launch.
+// mixed = true (fdl_refocus): a one-CTA check on the device sets the gate word to 1 when the
+// active requests all read one FDL of exactly H x W x C (the tiled path reuses its layers
+// across them), else 0; both paths are enqueued and the one the gate rules out returns at once.
+cudaError_t render_requests(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                            const RenderWs& w, cudaStream_t st, bool mixed, const float* shifts = nullptr) {
+  int* status = w.header + kStatusWord;
+  const int* gate = nullptr;
+  if (mixed && shifts == nullptr && render_fused_supported(H, W)) {
+    int* g = w.header + kGateWord;
+    cudaError_t e = launch_render_gate(req, B, count, C, H, W, Nmax, g, st);
+    if (e == cudaSuccess) e = launch_render_fused(req, B, count, C, H, W, Nmax, w.main, status, st, g);
+    if (e != cudaSuccess) return e;
+    gate = g;
+  }
+  cudaError_t e = launch_render_spectra(req, B, count, C, H, W, Nmax, render_spec_view(w.main, w.nyq, H, W), status,
+                                        st, shifts, gate);
+  if (e == cudaSuccess) e = render_inverse(w.main, w.nyq, w.tables, B, C, H, W, nullptr, req, count, st, Nmax, gate);
+  return e;
 }
 
 }  // namespace
@@ -406,15 +457,12 @@ FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H,
   if (B < 1 || C < 1 || C > 4 || N < 1 || N > 64 || !shape_ok(H, W)) return FDL_EINVAL;
   if (!layers || !d || !u0 || !out || !workspace) return FDL_EINVAL;
   if (workspace_bytes < fdl_render_workspace_size(B, C, H, W)) return FDL_ENOMEM;
+  if (B > 65535) return FDL_ENOTSUP;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Carver cv(workspace);
-  fdl_request* req = cv.take<fdl_request>(B);
-  float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
-  float2* nyq = cv.take<float2>((size_t)B * C * H);
-  float4* tables = cv.take<float4>(inv_table_elems(H, W));
-  cudaError_t e = launch_pinhole_requests(req, layers, d, N, u0, B, out, (long long)C * H * W, st);
-  if (e == cudaSuccess) e = launch_render_spectra(req, B, nullptr, C, H, W, N, render_spec_view(main, nyq, H, W), st);
-  if (e == cudaSuccess) e = render_inverse(main, nyq, tables, B, C, H, W, out, nullptr, nullptr, st);
+  const RenderWs w = carve_render(workspace, B, C, H, W, true);
+  cudaError_t e = cudaMemsetAsync(w.header, 0, kHeaderInts * sizeof(int), st);
+  if (e == cudaSuccess) e = launch_pinhole_requests(w.req, layers, d, N, C, H, W, u0, B, out, st);
+  if (e == cudaSuccess) e = render_requests(w.req, B, nullptr, C, H, W, N, w, st, false);
   return cuda_status(e);
 }
 
@@ -450,14 +498,25 @@ FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, 
   if (B < 1 || C < 1 || C > 4 || Nmax < 1 || Nmax > 64 || !shape_ok(H, W)) return FDL_EINVAL;
   if (!req || !workspace) return FDL_EINVAL;
   if (workspace_bytes < fdl_refocus_workspace_size(B, C, H, W)) return FDL_ENOMEM;
+  if (B > 65535) return FDL_ENOTSUP;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Carver cv(workspace);
-  float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
-  float2* nyq = cv.take<float2>((size_t)B * C * H);
-  float4* tables = cv.take<float4>(inv_table_elems(H, W));
-  cudaError_t e = launch_render_spectra(req, B, count, C, H, W, Nmax, render_spec_view(main, nyq, H, W), st);
-  if (e == cudaSuccess) e = render_inverse(main, nyq, tables, B, C, H, W, nullptr, req, count, st);
+  const RenderWs w = carve_render(workspace, B, C, H, W, false);
+  cudaError_t e = cudaMemsetAsync(w.header, 0, kHeaderInts * sizeof(int), st);
+  if (e == cudaSuccess) e = render_requests(req, B, count, C, H, W, Nmax, w, st, true);
   return cuda_status(e);
+}
+
+// ------------------------------------------------------------------ device status
+FDL_API int fdl_sync_status(const void* workspace, int* status, void* stream) {
+  if (!workspace || !status) return FDL_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, static_cast<const int*>(workspace) + kStatusWord, sizeof(int),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return FDL_ECUDA;
+  *status = v;
+  return FDL_OK;
 }
 
 // ------------------------------------------------------------------ calibration
@@ -546,9 +605,10 @@ FDL_API int fdl_fit_general(const float* spectra, int K, int C, int H, int W, in
   p.counters = f.counters;
   p.exp_table = f.exp_table;
   p.mom = nullptr;
-  cudaError_t e = cudaMemsetAsync(f.counters, 0, 16 * sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(f.counters, 0, kHeaderInts * sizeof(int), st);
   if (e == cudaSuccess) e = launch_exp_table(f.exp_table, st);
   if (e == cudaSuccess) e = launch_solve_hp(p, true, opts->precision == FDL_PREC_F64, 0, st);
+  if (e == cudaSuccess) e = launch_fit_status(f.counters, st);
   return cuda_status(e);
 }
 
@@ -563,16 +623,11 @@ FDL_API int fdl_render_shifts(const float* layers, const float* P, int N, int C,
   if (!layers || !P || !out || !workspace) return FDL_EINVAL;
   if (workspace_bytes < fdl_render_shifts_workspace_size(B, C, H, W)) return FDL_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Carver cv(workspace);
-  fdl_request* req = cv.take<fdl_request>(B);
-  float2* main = cv.take<float2>((size_t)B * C * H * (W / 2));
-  float2* nyq = cv.take<float2>((size_t)B * C * H);
-  float4* tables = cv.take<float4>(inv_table_elems(H, W));
+  const RenderWs w = carve_render(workspace, B, C, H, W, true);
+  cudaError_t e = cudaMemsetAsync(w.header, 0, kHeaderInts * sizeof(int), st);
   // pinhole requests on the FDL (d unused: the shifts replace u0 d_k)
-  cudaError_t e = launch_pinhole_requests(req, layers, P, N, nullptr, B, out, (long long)C * H * W, st);
-  if (e == cudaSuccess)
-    e = launch_render_spectra(req, B, nullptr, C, H, W, N, render_spec_view(main, nyq, H, W), st, P);
-  if (e == cudaSuccess) e = render_inverse(main, nyq, tables, B, C, H, W, out, nullptr, nullptr, st);
+  if (e == cudaSuccess) e = launch_pinhole_requests(w.req, layers, P, N, C, H, W, nullptr, B, out, st);
+  if (e == cudaSuccess) e = render_requests(w.req, B, nullptr, C, H, W, N, w, st, false, P);
   return cuda_status(e);
 }
 

@@ -15,124 +15,11 @@
 #include <utility>
 
 #include "kernels.h"
+#include "stockham.cuh"
 
 namespace fdl {
 
 namespace {
-
-// tw[t] = exp(-2 pi i t / L)
-__device__ __forceinline__ void make_twiddles(float2* tw, int L) {
-  for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    float s, c;
-    sincospif(-2.0f * (float)t / (float)L, &s, &c);
-    tw[t] = make_float2(c, s);
-  }
-}
-
-template <bool INV>
-__device__ __forceinline__ float2 twid(const float2* tw, int i) {
-  float2 w = tw[i];
-  if (INV) w.y = -w.y;
-  return w;
-}
-
-template <bool INV>
-__device__ __forceinline__ void radix4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = csub(a1, a3);
-  t3 = INV ? make_float2(-t3.y, t3.x) : make_float2(t3.y, -t3.x);  // times +i / -i
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
-}
-
-// In-place DFTs of `nfft` sequences of length L = 2^logL held in shared
-// memory at s[f * fstride + n * estride].  All threads of the CTA must call
-// it; each handles at most MAXB radix-4 butterflies per pass.
-template <bool INV, int MAXB>
-__device__ __forceinline__ void stockham(float2* s, const float2* tw, int L, int logL, int nfft,
-                                         int lognfft, int fstride, int estride) {
-  const int q = L >> 2;
-  const int logq = logL - 2;
-  const int total = nfft * q;
-  const bool fmajor = (fstride == 1);
-  int Ns = 1, logNs = 0;
-  for (int pass = 0; pass < (logL >> 1); ++pass) {
-    float2 v[MAXB][4];
-    int ob[MAXB];
-#pragma unroll
-    for (int b = 0; b < MAXB; ++b) {
-      const int task = threadIdx.x + b * blockDim.x;
-      if (task < total) {
-        int f, j;
-        if (fmajor) {
-          f = task & (nfft - 1);
-          j = task >> lognfft;
-        } else {
-          f = task >> logq;
-          j = task & (q - 1);
-        }
-        float2* p = s + f * fstride;
-        const int k = j & (Ns - 1);
-        float2 a0 = p[j * estride], a1 = p[(j + q) * estride];
-        float2 a2 = p[(j + 2 * q) * estride], a3 = p[(j + 3 * q) * estride];
-        if (pass > 0) {
-          const int step = k << (logq - logNs);  // k * L / (4 Ns)
-          a1 = cmul(a1, twid<INV>(tw, step));
-          a2 = cmul(a2, twid<INV>(tw, 2 * step));
-          a3 = cmul(a3, twid<INV>(tw, 3 * step));
-        }
-        radix4<INV>(a0, a1, a2, a3);
-        v[b][0] = a0;
-        v[b][1] = a1;
-        v[b][2] = a2;
-        v[b][3] = a3;
-        ob[b] = f * fstride + (((j - k) << 2) + k) * estride;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < MAXB; ++b) {
-      const int task = threadIdx.x + b * blockDim.x;
-      if (task < total) {
-        const int e = Ns * estride;
-        s[ob[b]] = v[b][0];
-        s[ob[b] + e] = v[b][1];
-        s[ob[b] + 2 * e] = v[b][2];
-        s[ob[b] + 3 * e] = v[b][3];
-      }
-    }
-    __syncthreads();
-    Ns <<= 2;
-    logNs += 2;
-  }
-  if (logL & 1) {
-    // last pass, radix 2 with Ns = L/2: reads and writes the same two slots.
-    const int h = L >> 1;
-    const int logh = logL - 1;
-    const int total2 = nfft * h;
-#pragma unroll
-    for (int b = 0; b < 2 * MAXB; ++b) {
-      const int task = threadIdx.x + b * blockDim.x;
-      if (task < total2) {
-        int f, j;
-        if (fmajor) {
-          f = task & (nfft - 1);
-          j = task >> lognfft;
-        } else {
-          f = task >> logh;
-          j = task & (h - 1);
-        }
-        float2* p = s + f * fstride;
-        float2 a0 = p[j * estride];
-        float2 a1 = cmul(p[(j + h) * estride], twid<INV>(tw, j));
-        p[j * estride] = cadd(a0, a1);
-        p[(j + h) * estride] = csub(a0, a1);
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------- row R2C
 // CTA of T = max(256, M/4) threads transforms R = T / (M/4) consecutive rows.
@@ -184,12 +71,16 @@ __global__ void __launch_bounds__(512) k_rfft_rows(const float* __restrict__ in,
 }
 
 // ---------------------------------------------------------------- row C2R
+constexpr int kMaxRowsPerCta = 128;  // R = max(256, M/4) / (M/4) with M >= 8
 template <int MAXB>
 __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ in, float* __restrict__ out,
                                                     long long nrows, int H, int W, int logM, float scale,
                                                     const fdl_request* __restrict__ req,
-                                                    const int* __restrict__ count, int C) {
+                                                    const int* __restrict__ count, int C, int nmax,
+                                                    const int* __restrict__ gate) {
   extern __shared__ float2 sm[];
+  __shared__ int rowok[kMaxRowsPerCta];
+  if (gate != nullptr && *gate == 0) return;
   const int M = W >> 1;
   float2* tw = sm;
   float2* data = sm + M;
@@ -199,6 +90,9 @@ __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ i
   if (count) nrows = min(nrows, (long long)(*count) * C * H);
   if (row0 >= nrows) return;
   make_twiddles(tw, M);
+  // rows of requests the render skipped are not written
+  for (int rr = threadIdx.x; rr < R; rr += blockDim.x)
+    rowok[rr] = req == nullptr || row0 + rr >= nrows || request_ok(req[(row0 + rr) / H / C], C, H, W, nmax, true);
   for (int e = threadIdx.x; e < R * M; e += blockDim.x) {
     const int r = e >> logM;
     float2 v = make_float2(0.f, 0.f);
@@ -246,6 +140,7 @@ __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ i
     v.z *= scale;
     v.w *= scale;
     const long long row = row0 + (e >> logW4);
+    if (!rowok[e >> logW4]) continue;
     float* rowp;
     if (req) {
       const long long img = row / H;
@@ -264,8 +159,10 @@ __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ i
 // CTA = one strip of SW columns of one image, all H rows, in shared memory.
 template <bool INV, int MAXB>
 __global__ void __launch_bounds__(512) k_fft_cols(SpecView in, SpecView out, int H, int logH, int W, int SW,
-                                                  int logSW, const int* __restrict__ count, int C) {
+                                                  int logSW, const int* __restrict__ count, int C,
+                                                  const int* __restrict__ gate) {
   extern __shared__ float2 sm[];
+  if (gate != nullptr && *gate == 0) return;
   float2* tw = sm;
   float2* data = sm + H;
   const int c0 = blockIdx.x * SW;
@@ -333,7 +230,7 @@ int strip_width(int H, int W) {
 
 template <bool INV>
 cudaError_t launch_cols(SpecView in, SpecView out, int nimg, int H, int W, const int* count, int C,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* gate = nullptr) {
   const int SW = strip_width(H, W);
   const int T = 512;
   const int bpt = (SW * H / 4 + T - 1) / T;  // butterflies per thread per pass
@@ -345,7 +242,7 @@ cudaError_t launch_cols(SpecView in, SpecView out, int nimg, int H, int W, const
   {                                                                                               \
     e = set_smem((const void*)k_fft_cols<INV, MB>, smem);                                         \
     if (e != cudaSuccess) return e;                                                               \
-    k_fft_cols<INV, MB><<<grid, T, smem, st>>>(in, out, H, logH, W, SW, logSW, count, C);         \
+    k_fft_cols<INV, MB><<<grid, T, smem, st>>>(in, out, H, logH, W, SW, logSW, count, C, gate);   \
   }
   if (bpt <= 1) FDL_COLS(1)
   else if (bpt <= 2) FDL_COLS(2)
@@ -390,7 +287,8 @@ cudaError_t launch_rfft_rows(const float* in, float2* out, long long nrows, int 
 }
 
 cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int H, int W, float scale,
-                              const fdl_request* req, const int* count, int C, cudaStream_t st) {
+                              const fdl_request* req, const int* count, int C, cudaStream_t st, int nmax,
+                              const int* gate) {
   const int M = W / 2;
   const int T = (M / 4 > 256) ? M / 4 : 256;
   const int R = T / (M / 4);
@@ -398,7 +296,8 @@ cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int
   const long long grid = (nrows + R - 1) / R;
   cudaError_t e = set_smem((const void*)k_irfft_rows<1>, smem);
   if (e != cudaSuccess) return e;
-  k_irfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, H, W, ilog2(M), scale, req, count, C);
+  k_irfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, H, W, ilog2(M), scale, req, count, C, nmax,
+                                                    gate);
   return cudaGetLastError();
 }
 
@@ -407,9 +306,9 @@ cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int 
 }
 
 cudaError_t launch_fft_cols_inv(SpecView in, float2* out, int nimg, int H, int W, const int* count, int C,
-                                cudaStream_t st) {
+                                cudaStream_t st, const int* gate) {
   SpecView o = spec_split(out, nullptr, H, W);
-  return launch_cols<true>(in, o, nimg, H, W, count, C, st);
+  return launch_cols<true>(in, o, nimg, H, W, count, C, st, gate);
 }
 
 }  // namespace fdl

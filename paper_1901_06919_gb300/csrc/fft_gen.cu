@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_rows_inv(SpecView in, float
                                                               long long nrows, int H, int W, int rpc, float scale,
                                                               const fdl_request* __restrict__ req,
                                                               const int* __restrict__ count, int C, GenPlan P,
-                                                              const float4* __restrict__ tab) {
+                                                              const float4* __restrict__ tab, int nmax) {
   extern __shared__ float4 sm[];
   const int Leff = P.M ? P.M : P.L;
   float4* a = sm;
@@ -270,7 +270,8 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_rows_inv(SpecView in, float
       const long long img = row / H;
       const int ky = (int)(row - img * H);
       const int bq = (int)(img / C), c = (int)(img - (long long)bq * C);
-      req[bq].out[((long long)c * H + ky) * W + n] = val;
+      // requests the render skipped are not written
+      if (request_ok(req[bq], C, H, W, nmax, true)) req[bq].out[((long long)c * H + ky) * W + n] = val;
     } else {
       out[row * W + n] = val;
     }
@@ -383,7 +384,7 @@ cudaError_t launch_gen_cols(SpecView s, SpecView so, int nimg, int H, int W, boo
 
 cudaError_t launch_gen_rows_inv(SpecView in, float* out, long long nrows, int H, int W, float scale,
                                 const fdl_request* req, const int* count, int C, const GenPlan& p, const float4* tab,
-                                cudaStream_t st) {
+                                cudaStream_t st, int nmax) {
   const int Leff = p.M ? p.M : p.L;
   const int rpc = seqs_per_cta(Leff);
   const size_t smem = rows_smem(Leff, rpc);
@@ -391,7 +392,7 @@ cudaError_t launch_gen_rows_inv(SpecView in, float* out, long long nrows, int H,
   if (e != cudaSuccess) return e;
   const long long grid = (nrows + rpc - 1) / rpc;
   k_gen_rows_inv<<<(unsigned)grid, kGenThreads, smem, st>>>(in, out, nrows, H, W, rpc, scale, req, count, C, p,
-                                                            tab);
+                                                            tab, nmax);
   return cudaGetLastError();
 }
 

@@ -24,8 +24,9 @@ cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int 
 // with pitch W/2 and the kx = 0 / kx = W/2 columns packed after taking
 // their Hermitian parts.
 // count (nullable, device): only images [0, *count * C) are transformed.
+// gate (nullable, device): the inverse passes return at once unless *gate != 0.
 cudaError_t launch_fft_cols_inv(SpecView in, float2* out, int nimg, int H, int W, const int* count, int C,
-                                cudaStream_t st);
+                                cudaStream_t st, const int* gate = nullptr);
 // The same forward passes with double-float arithmetic inside each pass
 // (fft_df.cu); `tables` = double-float twiddles of lengths W then H, built by
 // launch_twiddle_tables into fft_df_table_bytes(H, W) of workspace.
@@ -38,8 +39,10 @@ cudaError_t launch_fft_cols_fwd_df(SpecView in, SpecView out, int nimg, int H, i
 // Row pass of the inverse real DFT: packed rows (pitch W/2) -> W floats, times scale.
 // req (nullable, device): image b*C + c goes to req[b].out + c*H*W instead of
 // the contiguous `out`; count (nullable, device) limits the images to *count * C.
+// nmax: with req, rows of requests that request_ok(.., nmax, exact) rejects are not written.
 cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int H, int W, float scale,
-                              const fdl_request* req, const int* count, int C, cudaStream_t st);
+                              const fdl_request* req, const int* count, int C, cudaStream_t st, int nmax = 64,
+                              const int* gate = nullptr);
 
 // ---- per-frequency solve (solve.cu) -----------------------------------------
 struct SolveParams {
@@ -118,9 +121,41 @@ cudaError_t launch_gen_cols(SpecView s, SpecView so, int nimg, int H, int W, boo
 // Hermitian-completed inverse of the rows, real part x scale, to `out` or the requests' outputs
 cudaError_t launch_gen_rows_inv(SpecView in, float* out, long long nrows, int H, int W, float scale,
                                 const fdl_request* req, const int* count, int C, const GenPlan& pw,
-                                const float4* tables, cudaStream_t st);
+                                const float4* tables, cudaStream_t st, int nmax = 64);
+
+// A render request the kernels can serve: non-null, aligned FDL and output, 1 <= N <= Nmax <= 64,
+// a known aperture, finite parameters, and an image size within (C, H, W): equal to it
+// (exact: the general-length and fixed-size DFT paths) or any power-of-two size of at
+// least 16 within it (the fused power-of-two path).  Requests that fail are skipped
+// and set FDL_ST_BAD_REQUEST.
+__device__ __forceinline__ bool request_ok(const fdl_request& r, int C, int H, int W, int Nmax, bool exact) {
+  if (r.layers == nullptr || r.d == nullptr || r.out == nullptr) return false;
+  // complex64 layers and tables, float32 d; output rows whose width is a multiple of 4 are
+  // written as float4
+  const uintptr_t out_align = (r.W & 3) == 0 ? 15 : 3;
+  if (((uintptr_t)r.layers & 7) != 0 || ((uintptr_t)r.d & 3) != 0 || ((uintptr_t)r.out & out_align) != 0 ||
+      ((uintptr_t)r.pts & 7) != 0)
+    return false;
+  if (r.N < 1 || r.N > Nmax || r.N > 64) return false;
+  if (r.aperture < FDL_AP_PINHOLE || r.aperture > FDL_AP_TABLE) return false;
+  if ((r.aperture == FDL_AP_POINTS || r.aperture == FDL_AP_TABLE) && r.npts > 0 && r.pts == nullptr) return false;
+  if (r.npts < 0 || !(r.radius >= 0.f) || !isfinite(r.radius) || !isfinite(r.u0x) || !isfinite(r.u0y) ||
+      !isfinite(r.s))
+    return false;
+  if (exact) return r.H == H && r.W == W && r.C == C;
+  const bool p2 = r.H >= 16 && r.W >= 16 && (r.H & (r.H - 1)) == 0 && (r.W & (r.W - 1)) == 0;
+  return p2 && r.H <= H && r.W <= W && r.C >= 1 && r.C <= C;
+}
+
+// Every workspace starts with kHeaderInts ints: the counters of a fit and, at index
+// kStatusWord, the device status word (FDL_ST_* bits) that fdl_sync_status reads.
+constexpr int kHeaderInts = 16;
+constexpr int kStatusWord = 15;
+constexpr int kGateWord = 14;  // renders: 1 = the tiled path serves the batch, 0 = the fused path
 
 // ---- tier selection (select.cu) ---------------------------------------------
+// sets the status word of a fit from its breakdown and non-finite counters
+cudaError_t launch_fit_status(int* counters, cudaStream_t st);
 // Appends to `list` the frequencies with the largest err so that the rest keep
 // u * sqrt(sum err^2) <= budget * sqrt(sum xn2); scratch of select_scratch_bytes().
 size_t select_scratch_bytes();
@@ -132,13 +167,30 @@ cudaError_t launch_select_budget(const float* err, const float* xn2, int n, doub
 // requests read one FDL.
 // shifts: optional [B][N][2] per-layer shifts of each request (the relaxed model's P_jk
 // instead of u0 d_k; pinhole requests)
+// gate (nullable, device): returns at once unless *gate != 0 (see launch_render_gate).
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                                  SpecView out, cudaStream_t st, const float* shifts = nullptr);
+                                  SpecView out, int* status, cudaStream_t st, const float* shifts = nullptr,
+                                  const int* gate = nullptr);
+// *gate = 1 when every active request is valid, reads the same FDL (layers, d, N) and has
+// exactly the size (C, H, W): the tiled path (layer values staged once per tile of
+// frequencies and reused by every request) serves it; otherwise 0 and the fused path does.
+cudaError_t launch_render_gate(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                               int* gate, cudaStream_t st);
 // drawn aperture: centred zero-padded raster and its sum (double), then the table scaling
 cudaError_t launch_aperture_table_prep(const float* R, int P, int Z, float* pad, double* sum, cudaStream_t st);
 cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cudaStream_t st);
-cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N,
-                                    const float* u0, int B, float* out, long long img_elems, cudaStream_t st);
+cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N, int C, int H,
+                                    int W, const float* u0, int B, float* out, cudaStream_t st);
+// Fused render of power-of-two sizes up to 2048 x 4096 (requests of different sizes
+// within (C, H, W) may share the launch): Eq. BsFourier evaluated for a strip of columns
+// straight into shared memory, the inverse column DFT there, the strip written to
+// request b's slot of `slots` (split layout, pitch W_b/2, slot_elems complex per
+// request); then the inverse row DFT from the slots into the requests' outputs.
+bool render_fused_supported(int H, int W);
+size_t render_fused_slot_elems(int C, int H, int W);
+// gate (nullable, device): returns at once when *gate != 0.
+cudaError_t launch_render_fused(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                                float2* slots, int* status, cudaStream_t st, const int* gate = nullptr);
 
 // ---- calibration (calib.cu) -------------------------------------------------
 struct CalibParams {

@@ -5,6 +5,7 @@
 // inverse column and row DFT passes.  psi is normalised to integrate to 1,
 // so psi_hat(0) = 1 and a pinhole (psi = delta) gives psi_hat = 1 (Sec. IV-B).
 #include "hp_solve.cuh"
+#include "stockham.cuh"
 
 namespace fdl {
 
@@ -165,22 +166,24 @@ __device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, in
 }
 
 // the request's terms with the loop specialised for where the layers live, the shift model
-// and the aperture kind (all uniform over the request)
+// and the aperture kind (all uniform over the request).  The phase factor is evaluated
+// directly at every layer here: a recurrence across layers measured slower in this kernel
+// (a dependent chain per warp and request, and its set-up for the few layers each warp
+// takes when the layers of one request are split across warps).
 __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                              float wx, float wabs, long long plane, long long off, bool valid,
                                              const float2* tile, const float* dsh, int lane, float2 acc[4],
                                              const float2* __restrict__ shb, const Freq& fq) {
+#define FDL_AP(T, S) render_terms_ap<T, S>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, \
+                                          shb, fq)
   if (tile != nullptr) {
-    if (shb != nullptr)
-      render_terms_ap<true, true>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
-    else
-      render_terms_ap<true, false>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
+    if (shb != nullptr) FDL_AP(true, true);
+    else FDL_AP(true, false);
   } else {
-    if (shb != nullptr)
-      render_terms_ap<false, true>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
-    else
-      render_terms_ap<false, false>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq);
+    if (shb != nullptr) FDL_AP(false, true);
+    else FDL_AP(false, false);
   }
+#undef FDL_AP
 }
 
 // CTA: 32 consecutive stored bins (lane = bin) x 8 warps.
@@ -192,11 +195,14 @@ __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int k
 //    still occupies the whole CTA.
 __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request* __restrict__ req, int B,
                                                               const int* __restrict__ count, int C, int H, int W,
-                                                              int tile_lc, SpecView out, const float* __restrict__ shifts) {
+                                                              int tile_lc, int nmax, SpecView out,
+                                                              const float* __restrict__ shifts, int* __restrict__ status,
+                                                              const int* __restrict__ gate) {
   extern __shared__ float2 tile[];  // [tile_lc][32]
   __shared__ float dsh[64];
   __shared__ float2 part[kRenderWarps][4][32];
   __shared__ int uniform;
+  if (gate != nullptr && *gate == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = W >> 1;
   const int Qs = H * (M + 1);
@@ -219,7 +225,9 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
-    if (b < Bact) {
+    const bool rok = b < Bact && request_ok(req[b], C, H, W, nmax, true);
+    if (b < Bact && !rok && blockIdx.x == 0 && sl == 0 && lane == 0) atomicOr(status, FDL_ST_BAD_REQUEST);
+    if (rok) {
       const fdl_request r = req[b];
       const df theta = df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, wxlo, r.u0y * wylo));
       const float2* shb = shifts ? reinterpret_cast<const float2*>(shifts) + (long long)b * r.N : nullptr;
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
 #pragma unroll
     for (int c = 0; c < 4; ++c) part[warp][c][lane] = acc[c];
     __syncthreads();
-    if (b < Bact && sl == 0 && valid) {
+    if (rok && sl == 0 && valid) {
       for (int w = 1; w < G; ++w) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] = cadd(acc[c], part[warp + w][c][lane]);
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   const float* L0 = req[0].layers;
   const int N0 = req[0].N;
   for (int b = threadIdx.x; b < Bact; b += blockDim.x)
-    if (req[b].layers != L0 || req[b].d != req[0].d) uniform = 0;
+    if (req[b].layers != L0 || req[b].d != req[0].d || !request_ok(req[b], C, H, W, nmax, true)) uniform = 0;
   __syncthreads();
   const bool shared = uniform && N0 * C <= tile_lc && N0 <= 64;
   if (shared) {
@@ -265,6 +273,10 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
     __syncthreads();
   }
   for (int b = warp; b < Bact; b += kRenderWarps) {
+    if (!request_ok(req[b], C, H, W, nmax, true)) {
+      if (blockIdx.x == 0 && lane == 0) atomicOr(status, FDL_ST_BAD_REQUEST);
+      continue;
+    }
     const fdl_request r = req[b];
     const df theta = df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, wxlo, r.u0y * wylo));
     float2 acc[4];
@@ -281,14 +293,36 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   }
 }
 
-__global__ void k_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N,
-                                   const float* u0, int B, float* out, long long img_elems) {
+// *gate = 1 when every active request passes request_ok with exactly (C, H, W) and reads the
+// same FDL (layers, d, N) as request 0, else 0.
+__global__ void __launch_bounds__(256) k_render_gate(const fdl_request* __restrict__ req, int B,
+                                                     const int* __restrict__ count, int C, int H, int W, int Nmax,
+                                                     int* __restrict__ gate) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = 1;
+  __syncthreads();
+  const int Bact = count ? min(*count, B) : B;
+  for (int b = threadIdx.x; b < Bact; b += blockDim.x) {
+    const fdl_request& r = req[b];
+    if (!request_ok(r, C, H, W, Nmax, true) || r.layers != req[0].layers || r.d != req[0].d || r.N != req[0].N)
+      ok = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *gate = ok;
+}
+
+__global__ void k_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N, int C, int H,
+                                   int W, const float* u0, int B, float* out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   fdl_request r;
   r.layers = layers;
   r.d = d;
-  r.out = out + (long long)b * img_elems;
+  r.out = out + (long long)b * C * H * W;
+  r.H = H;
+  r.W = W;
+  r.C = C;
+  r.pad_[0] = r.pad_[1] = 0;
   r.pts = nullptr;
   r.N = N;
   r.npts = 0;
@@ -297,7 +331,6 @@ __global__ void k_pinhole_requests(fdl_request* req, const float* layers, const 
   r.u0y = u0 ? u0[2 * b + 1] : 0.f;
   r.s = 0.f;
   r.radius = 0.f;
-  r.pad_ = 0;
   req[b] = r;
 }
 
@@ -336,6 +369,285 @@ __global__ void k_scale_table(float2* __restrict__ T, long long n, const double*
     T[e] = make_float2(T[e].x * inv, T[e].y * inv);
 }
 
+// ------------------------------------------------------------ fused power-of-two path
+// One CTA renders a strip of SW columns of one request's half spectrum (all H rows) by
+// Eq. BsFourier straight into shared memory, runs the inverse DFT along y there and
+// writes the strip in the split layout of the row pass: the rendered spectrum itself
+// never reaches HBM.  Requests of different power-of-two sizes share a launch: each CTA
+// takes its request's H, W, C, N from the descriptor (grid sized for the largest).
+constexpr int kRcThreads = 256;
+constexpr int kRcFreqs = 2048;  // H * SW of a CTA's strip (the strip of one column when H > 2048 is not used)
+constexpr int kRcMaxH = 2048;
+
+// columns per strip for an image of H rows and M = W/2 stored columns below the Nyquist one
+__host__ __device__ __forceinline__ int rc_strip(int H, int M) {
+  int sw = kRcFreqs / H;
+  if (sw < 1) sw = 1;
+  if (sw > M) sw = M;
+  return sw;
+}
+
+__device__ __forceinline__ int log2_pow2(int v) { return 31 - __clz(v); }
+
+// Terms of Eq. BsFourier over the layers at one frequency: acc[c] += exp(+2 pi i d_k (u0 . w))
+// psi_hat((s - d_k) w) x_kc(w).  REC (disparities on a grid d_k = d_0 + k delta, deviations
+// within the check of the caller): the phase factor advances by exp(2 pi i delta (u0 . w))
+// from layer to layer and is evaluated directly every 8 layers; otherwise it is evaluated
+// at every layer.  AP as in render_terms_t.
+template <int AP, bool REC>
+__device__ __forceinline__ void rc_layers(const fdl_request& r, const float* dsh, float delta, int N, int C,
+                                          const float2* __restrict__ x, long long plane, long long off, df theta,
+                                          float wy, float wx, float wabs, float2 acc[4]) {
+  float2 step = make_float2(1.f, 0.f), cur = make_float2(1.f, 0.f);
+  if (REC) {
+    float sn, cs;
+    sincospif(2.f * phase_from_theta(theta, delta), &sn, &cs);
+    step = make_float2(cs, sn);
+  }
+  const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
+#pragma unroll 4
+  for (int k = 0; k < N; ++k) {
+    const float dk = dsh[k];
+    // |2 pi ph| <= pi: the hardware sine and cosine (absolute error about 2^-21 there)
+    if (!REC || (k & 7) == 0) __sincosf(6.28318531f * phase_from_theta(theta, dk), &cur.y, &cur.x);
+    float2 coef = cur;
+    if constexpr (AP == 1) {
+      coef = cscale(coef, disc_hat(zscale * fabsf(r.s - dk)));
+    } else if constexpr (AP == 2) {
+      const float sd = r.s - dk;
+      coef = cmul(coef, aperture_table_hat(reinterpret_cast<const float2*>(r.pts), r.npts, r.radius, sd * wy, sd * wx));
+    } else if constexpr (AP == 3) {
+      const float sd = r.s - dk;
+      coef = cmul(coef, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
+    }
+    const float2* xk = x + (long long)k * C * plane + off;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < C) cfma(acc[c], coef, __ldg(xk + (long long)c * plane));
+    if (REC) cur = cmul(cur, step);
+  }
+}
+
+__device__ __forceinline__ void rc_render_freq(const fdl_request& r, int ap, bool rec, const float* dsh, float delta,
+                                               int N, int C, const float2* __restrict__ x, long long plane,
+                                               long long off, df theta, float wy, float wx, float wabs,
+                                               float2 acc[4]) {
+#define FDL_RC(A, RE) rc_layers<A, RE>(r, dsh, delta, N, C, x, plane, off, theta, wy, wx, wabs, acc)
+  if (rec) {
+    if (ap == 0) FDL_RC(0, true);
+    else if (ap == 1) FDL_RC(1, true);
+    else if (ap == 2) FDL_RC(2, true);
+    else FDL_RC(3, true);
+  } else {
+    if (ap == 0) FDL_RC(0, false);
+    else if (ap == 1) FDL_RC(1, false);
+    else if (ap == 2) FDL_RC(2, false);
+    else FDL_RC(3, false);
+  }
+#undef FDL_RC
+}
+
+// FIRST: column 0 and the Nyquist column kx = W/2 of every request, packed as Herm(F0) +
+// i Herm(FN) before the inverse DFT (the split layout's element 0 of each row); otherwise
+// strip blockIdx.y of SW columns (column 0 of strip 0 is left to the FIRST launch).
+// Request b = blockIdx.x, so consecutive CTAs render the same strip of different requests
+// and the layer values of the strip stay in L2 between them.
+template <bool FIRST>
+__global__ void __launch_bounds__(kRcThreads) k_render_cols(const fdl_request* __restrict__ req,
+                                                            const int* __restrict__ count, int Cmax, int Hmax,
+                                                            int Wmax, int Nmax, float2* __restrict__ slots,
+                                                            long long slot_elems, int* __restrict__ status,
+                                                            const int* __restrict__ gate) {
+  extern __shared__ float2 sm[];
+  __shared__ float dsh[64];
+  __shared__ float sdelta;
+  __shared__ int srec;
+  const int b = blockIdx.x;
+  if (gate != nullptr && *gate != 0) return;
+  if (count != nullptr && b >= *count) return;
+  const fdl_request r = req[b];
+  if (!request_ok(r, Cmax, Hmax, Wmax, Nmax, false)) {
+    if (FIRST && threadIdx.x == 0) atomicOr(status, FDL_ST_BAD_REQUEST);
+    return;
+  }
+  const int H = r.H, W = r.W, C = r.C, N = r.N, M = W >> 1;
+  const int SW = FIRST ? 1 : rc_strip(H, M);
+  const int c0 = FIRST ? 0 : (int)blockIdx.y * SW;
+  if (c0 >= M) return;
+  const int logH = log2_pow2(H), logSW = log2_pow2(SW);
+  const int HS = H * SW;
+  float2* tw = sm;           // [H]
+  float2* data = sm + Hmax;  // [C][H][SW]
+  float2* nyq = data + (long long)Cmax * Hmax;  // FIRST: [C][H], the Nyquist column
+  for (int k = threadIdx.x; k < N; k += blockDim.x) dsh[k] = __ldg(r.d + k);
+  make_twiddles(tw, H);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // the grid the recurrence follows and the largest deviation from it
+    const float delta = N > 1 ? (dsh[N - 1] - dsh[0]) / (float)(N - 1) : 0.f;
+    float em = 0.f;
+    for (int k = threadIdx.x; k < N; k += 32)
+      em = fmaxf(em, fabsf((float)((double)dsh[k] - (double)dsh[0] - (double)k * (double)delta)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+    if (threadIdx.x == 0) {
+      // |w_x|, |w_y| <= 1/2: the phase of the factor drifts from the exact one by at most
+      // 2 pi (2 em) (|u0x| + |u0y|) / 2 between two direct evaluations
+      const float drift = 6.2831853f * em * (fabsf(r.u0x) + fabsf(r.u0y));
+      sdelta = delta;
+      srec = (N >= 2 && isfinite(delta) && drift <= 2e-6f) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  const float delta = sdelta;
+  const bool rec = srec != 0;
+  const int ap = (r.aperture == FDL_AP_PINHOLE || (r.aperture == FDL_AP_DISC && r.radius == 0.f)) ? 0
+                 : r.aperture == FDL_AP_DISC                                                  ? 1
+                 : r.aperture == FDL_AP_TABLE                                                 ? 2
+                                                                                              : 3;
+  const float2* x = reinterpret_cast<const float2*>(r.layers);
+  const long long plane = (long long)H * (M + 1);
+  const int nf = FIRST ? 2 * H : HS;
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    int ky, kx;
+    if (FIRST) {
+      ky = f < H ? f : f - H;
+      kx = f < H ? 0 : M;
+    } else {
+      ky = f >> logSW;
+      kx = c0 + (f & (SW - 1));
+    }
+    float2 acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+    if (FIRST || kx != 0) {
+      const Freq fq = bin_freq(ky, kx, H, W);
+      const df theta =
+          df_add_f(df_add(two_prod(r.u0x, fq.wx), two_prod(r.u0y, fq.wy)), fmaf(r.u0x, fq.wx_lo, r.u0y * fq.wy_lo));
+      const float wabs = sqrtf(fq.wx * fq.wx + fq.wy * fq.wy);
+      rc_render_freq(r, ap, rec, dsh, delta, N, C, x, plane, (long long)ky * (M + 1) + kx, theta, fq.wy, fq.wx, wabs,
+                     acc);
+    }
+    if (FIRST) {
+      float2* dst = f < H ? data + ky : nyq + ky;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < C) dst[c * H] = acc[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < C) data[c * HS + f] = acc[c];
+    }
+  }
+  __syncthreads();
+  if (FIRST) {
+    // column 0 <- Herm(F0) + i Herm(FN), Herm(F)[ky] = (F[ky] + conj F[-ky]) / 2
+    for (int c = 0; c < C; ++c) {
+      constexpr int kRows = kRcMaxH / kRcThreads;
+      float2 pk[kRows];
+#pragma unroll
+      for (int i = 0; i < kRows; ++i) {
+        const int ky = threadIdx.x + i * kRcThreads;
+        if (ky < H) {
+          const int km = (H - ky) & (H - 1);
+          const float2 f0 = data[c * H + ky], f0m = data[c * H + km];
+          const float2 fn = nyq[c * H + ky], fnm = nyq[c * H + km];
+          const float2 h0 = make_float2(0.5f * (f0.x + f0m.x), 0.5f * (f0.y - f0m.y));
+          const float2 hn = make_float2(0.5f * (fn.x + fnm.x), 0.5f * (fn.y - fnm.y));
+          pk[i] = make_float2(h0.x - hn.y, h0.y + hn.x);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < kRows; ++i) {
+        const int ky = threadIdx.x + i * kRcThreads;
+        if (ky < H) data[c * H + ky] = pk[i];
+      }
+      __syncthreads();
+    }
+  }
+  for (int c = 0; c < C; ++c) stockham<true, 2>(data + c * HS, tw, H, logH, SW, logSW, 1, SW);
+  float2* dst = slots + (long long)b * slot_elems;
+  for (int f = threadIdx.x; f < HS; f += blockDim.x) {
+    const int ky = f >> logSW, kx = c0 + (f & (SW - 1));
+    if (!FIRST && kx == 0) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < C) dst[((long long)c * H + ky) * M + kx] = data[c * HS + f];
+  }
+}
+
+// Inverse row DFT of the fused path: rows of request b's slot (pitch M = W_b/2, element 0
+// packing X[0] + i X[W/2]) -> the request's output, times 1 / (H W).  A CTA takes
+// kRcFreqs / M consecutive rows of one request.
+__global__ void __launch_bounds__(kRcThreads) k_irfft_rows_req(const fdl_request* __restrict__ req,
+                                                               const int* __restrict__ count, int Cmax, int Hmax,
+                                                               int Wmax, int Nmax, const float2* __restrict__ slots,
+                                                               long long slot_elems, const int* __restrict__ gate) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  if (gate != nullptr && *gate != 0) return;
+  if (count != nullptr && b >= *count) return;
+  const fdl_request r = req[b];
+  if (!request_ok(r, Cmax, Hmax, Wmax, Nmax, false)) return;
+  const int H = r.H, W = r.W, C = r.C, M = W >> 1, logM = log2_pow2(M);
+  const int R = kRcFreqs / M;  // M <= 2048
+  const long long nrows = (long long)C * H;
+  const long long row0 = (long long)blockIdx.x * R;
+  if (row0 >= nrows) return;
+  float2* tw = sm;
+  float2* data = sm + (Wmax >> 1);
+  make_twiddles(tw, M);
+  const float2* in = slots + (long long)b * slot_elems;
+  for (int e = threadIdx.x; e < R * M; e += blockDim.x) {
+    const int rr = e >> logM;
+    data[e] = row0 + rr < nrows ? in[(row0 + rr) * M + (e & (M - 1))] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // Z[k] = E[k] + i O[k], E[k] = X[k] + conj X[M-k],
+  // O[k] = (X[k] - conj X[M-k]) exp(+2 pi i k / W); X[0], X[M] are packed in element 0.
+  constexpr int kPer = kRcFreqs / kRcThreads;  // R * M = kRcFreqs elements, kPer per thread
+  float2 zk[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int e = threadIdx.x + i * kRcThreads;
+    const int rr = e >> logM, k = e & (M - 1);
+    const float2* X = data + rr * M;
+    float2 Z;
+    if (k == 0) {
+      const float x0 = X[0].x, xm = X[0].y;
+      Z = make_float2(x0 + xm, x0 - xm);
+    } else {
+      const float2 a = X[k], bm = X[M - k];
+      const float2 E = make_float2(a.x + bm.x, a.y - bm.y);
+      float2 O = make_float2(a.x - bm.x, a.y + bm.y);
+      float sn, cs;
+      sincospif((float)k / (float)M, &sn, &cs);
+      O = cmul(O, make_float2(cs, sn));
+      Z = make_float2(E.x - O.y, E.y + O.x);
+    }
+    zk[i] = Z;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) data[threadIdx.x + i * kRcThreads] = zk[i];
+  __syncthreads();
+  stockham<true, 2>(data, tw, M, logM, R, log2_pow2(R), M, 1);
+  const float scale = 1.f / ((float)H * (float)W);
+  const long long rows_here = min((long long)R, nrows - row0);
+  const int valid = (int)rows_here * (W >> 2);
+  const int logW4 = logM - 1;
+  for (int e = threadIdx.x; e < valid; e += blockDim.x) {
+    float4 v = reinterpret_cast<const float4*>(data)[e];
+    v.x *= scale;
+    v.y *= scale;
+    v.z *= scale;
+    v.w *= scale;
+    const long long row = row0 + (e >> logW4);
+    reinterpret_cast<float4*>(r.out + row * W)[e & ((W >> 2) - 1)] = v;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_aperture_table_prep(const float* R, int P, int Z, float* pad, double* sum, cudaStream_t st) {
@@ -351,20 +663,57 @@ cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cud
   return cudaGetLastError();
 }
 
+cudaError_t launch_render_gate(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                               int* gate, cudaStream_t st) {
+  k_render_gate<<<1, 256, 0, st>>>(req, B, count, C, H, W, Nmax, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                                  SpecView out, cudaStream_t st, const float* shifts) {
+                                  SpecView out, int* status, cudaStream_t st, const float* shifts, const int* gate) {
   const int Qs = H * (W / 2 + 1);
   const int tile_lc = min(Nmax * C, kTileMaxLC);
   const size_t smem = (size_t)tile_lc * 32 * sizeof(float2);
   cudaError_t e = set_smem((const void*)k_render, (size_t)kTileMaxLC * 32 * sizeof(float2));
   if (e != cudaSuccess) return e;
-  k_render<<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, out, shifts);
+  k_render<<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, Nmax, out, shifts,
+                                                            status, gate);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N,
-                                    const float* u0, int B, float* out, long long img_elems, cudaStream_t st) {
-  k_pinhole_requests<<<(B + 127) / 128, 128, 0, st>>>(req, layers, d, N, u0, B, out, img_elems);
+cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N, int C, int H,
+                                    int W, const float* u0, int B, float* out, cudaStream_t st) {
+  k_pinhole_requests<<<(B + 127) / 128, 128, 0, st>>>(req, layers, d, N, C, H, W, u0, B, out);
+  return cudaGetLastError();
+}
+
+bool render_fused_supported(int H, int W) {
+  auto p2 = [](int v) { return v >= 16 && (v & (v - 1)) == 0; };
+  return p2(H) && p2(W) && H <= kRcMaxH && W <= 4096;
+}
+
+size_t render_fused_slot_elems(int C, int H, int W) { return (size_t)C * H * (W / 2); }
+
+cudaError_t launch_render_fused(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                                float2* slots, int* status, cudaStream_t st, const int* gate) {
+  if (!render_fused_supported(H, W) || B < 1 || B > 65535) return cudaErrorInvalidValue;
+  const long long se = (long long)render_fused_slot_elems(C, H, W);
+  const int M = W / 2;
+  // a request within (C, H, W) has at most as many strips and row blocks as one of that size
+  const int strips = M / rc_strip(H, M);
+  const long long row_blocks = ((long long)C * H * M + kRcFreqs - 1) / kRcFreqs;
+  const size_t smem_main = (size_t)(H + (size_t)C * (H > kRcFreqs ? H : kRcFreqs)) * sizeof(float2);
+  const size_t smem_first = (size_t)(H + 2 * (size_t)C * H) * sizeof(float2);
+  const size_t smem_rows = (size_t)(M + kRcFreqs) * sizeof(float2);
+  cudaError_t e = set_smem((const void*)k_render_cols<false>, smem_main);
+  if (e == cudaSuccess) e = set_smem((const void*)k_render_cols<true>, smem_first);
+  if (e == cudaSuccess) e = set_smem((const void*)k_irfft_rows_req, smem_rows);
+  if (e != cudaSuccess) return e;
+  k_render_cols<false><<<dim3(B, strips), kRcThreads, smem_main, st>>>(req, count, C, H, W, Nmax, slots, se, status,
+                                                                        gate);
+  k_render_cols<true><<<dim3(B, 1), kRcThreads, smem_first, st>>>(req, count, C, H, W, Nmax, slots, se, status, gate);
+  k_irfft_rows_req<<<dim3((unsigned)row_blocks, B), kRcThreads, smem_rows, st>>>(req, count, C, H, W, Nmax, slots,
+                                                                                 se, gate);
   return cudaGetLastError();
 }
 

@@ -122,7 +122,20 @@ __global__ void k_err_compact(const float* __restrict__ err, int n, const float*
   }
 }
 
+// status word of a fit: the bits of the counters the solve passes left behind
+__global__ void k_fit_status(int* counters) {
+  int st = counters[kStatusWord];
+  if (counters[2] > 0) st |= FDL_ST_BREAKDOWN;
+  if (counters[3] > 0) st |= FDL_ST_NONFINITE;
+  counters[kStatusWord] = st;
+}
+
 }  // namespace
+
+cudaError_t launch_fit_status(int* counters, cudaStream_t st) {
+  k_fit_status<<<1, 1, 0, st>>>(counters);
+  return cudaGetLastError();
+}
 
 size_t select_scratch_bytes() { return kBuckets * (sizeof(double) + sizeof(unsigned int)) + 64; }
 

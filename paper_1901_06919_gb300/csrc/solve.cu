@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, 
   cx<T>* Y = Arow + N;
   const int* lst = list == 0 ? sp.flagged : sp.flagged64;
   const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(sp.counters + (list == 0 ? 4 : 5)));
-  int nhp = 0, nbad = 0;
+  int nhp = 0, nbad = 0, nfixed = 0, nnf = 0;
   for (int li = blockIdx.x * warps + warp; li < total; li += gridDim.x * warps) {
     const int q = all_bins ? li : lst[li];
     int ky, kx;
@@ -317,15 +317,21 @@ __global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, 
     const bool ok = hp_solve_bin<T>(p, ky, kx, G, Arow, Y);
     const long long plane = (long long)p.H * (M + 1);
     const long long off = (long long)ky * (M + 1) + kx;
+    bool fin = true;
     for (int e = lane; e < N * C; e += 32) {
       const int r = e / C, c = e - r * C;
       const cx<T> v = Y[e];
-      sp.x[((long long)r * C + c) * plane + off] =
-          ok ? make_float2(r_to_float(v.re), r_to_float(v.im)) : make_float2(0.f, 0.f);
+      const float2 xv = ok ? make_float2(r_to_float(v.re), r_to_float(v.im)) : make_float2(0.f, 0.f);
+      fin = fin && isfinite(xv.x) && isfinite(xv.y);
+      sp.x[((long long)r * C + c) * plane + off] = xv;
     }
+    fin = __all_sync(0xffffffffu, fin);
     if (lane == 0) {
       ++nhp;
       if (!ok) ++nbad;
+      // the double-float pass marked its breakdowns with err = +inf and counted them
+      if (list == 1 && sp.err != nullptr && isinf(sp.err[q])) ++nfixed;
+      if (!fin && all_bins) ++nnf;
     }
     __syncwarp();
   }
@@ -334,6 +340,8 @@ __global__ void __launch_bounds__(128) k_solve_hp(SolveParams sp, int all_bins, 
     // a frequency re-solved from the FP64 list was counted by the double-float pass
     if (nhp && list == 1) atomicSub(sp.counters + 1, nhp);
     if (nbad) atomicAdd(sp.counters + 2, nbad);
+    if (nfixed) atomicSub(sp.counters + 2, nfixed);
+    if (nnf) atomicAdd(sp.counters + 3, nnf);
   }
 }
 

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
   for (int h = 0; h < R; ++h) em[h] = (MOM && lane + 32 * h < N) ? p.mom[lane + 32 * h] : make_float2(0.f, 0.f);
   const float4* tab = p.exp_table;
   const int total = all_bins ? p.H * (M + 1) : *((volatile int*)(p.counters + 4));
-  int nhp = 0, nbad = 0;
+  int nhp = 0, nbad = 0, nnf = 0;
   for (int li = blockIdx.x * kDfWarps + warp; li < total; li += gridDim.x * kDfWarps) {
     const int q = all_bins ? li : p.flagged[li];
     int ky, kx;
@@ -761,6 +761,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
     const long long plane = (long long)p.H * (M + 1);
     const long long off = (long long)ky * (M + 1) + kx;
     float n2 = 0.f;
+    bool fin = true;
 #pragma unroll
     for (int h = 0; h < R; ++h) {
       const int r = lane + 32 * h;
@@ -772,9 +773,14 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
                 ok ? make_float2(y[h][c].re.hi + y[h][c].re.lo, y[h][c].im.hi + y[h][c].im.lo) : make_float2(0.f, 0.f);
             p.x[((long long)r * C + c) * plane + off] = xv;
             n2 += xv.x * xv.x + xv.y * xv.y;
+            fin = fin && isfinite(xv.x) && isfinite(xv.y);
           }
       }
     }
+    // a non-finite input reaches the solution (A and Gamma are finite): counted by the
+    // first pass over all frequencies (a listed frequency was counted by the FP32 pass)
+    fin = __all_sync(0xffffffffu, fin);
+    if (!fin && all_bins && lane == 0) ++nnf;
     if (p.err != nullptr) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
@@ -796,6 +802,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
     // a listed frequency was first solved (and counted) by the FP32 pass
     if (nhp && !all_bins) atomicSub(p.counters + 0, nhp);
     if (nbad) atomicAdd(p.counters + 2, nbad);
+    if (nnf) atomicAdd(p.counters + 3, nnf);
   }
 }
 

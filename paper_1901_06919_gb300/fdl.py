@@ -96,6 +96,10 @@ class FitWorkspace:
         return {"fp32": c[0], "df": c[1], "fp64": c[2], "high_precision": c[1] + c[2], "breakdown": c[3],
                 "nonfinite": c[4]}
 
+    def status(self, stream=None) -> int:
+        """Device status word of the last fit (``L.ST_*`` bits); synchronises the stream."""
+        return sync_status(self, stream)
+
 
 def fit(views: torch.Tensor, u: torch.Tensor, d: torch.Tensor, lam: float, eps: float = 1e-4,
         reg: str = "view2", precision: str = "mixed", kappa_max: float = 0.0,
@@ -189,20 +193,33 @@ def pack_requests(specs: list[RenderSpec], device) -> torch.Tensor:
         arr[i] = L.Request(sp.layers.data_ptr(), sp.d.data_ptr(), sp.out.data_ptr(),
                            sp.pts.data_ptr() if sp.pts is not None else None, N,
                            0 if sp.pts is None else sp.pts.shape[0], L.APERTURE[sp.aperture],
-                           float(sp.u0[0]), float(sp.u0[1]), float(sp.s), float(sp.radius), 0)
+                           float(sp.u0[0]), float(sp.u0[1]), float(sp.s), float(sp.radius), H,
+                           _width(Wh, sp.W), C)
     host = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
     return host.to(device)
 
 
 def refocus(req_dev: torch.Tensor, B: int, C: int, H: int, W: int, Nmax: int, count: torch.Tensor | None = None,
-            ws: torch.Tensor | None = None, stream=None) -> None:
-    """Render B requests (device array from :func:`pack_requests`) into their outputs."""
+            ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Render B requests (device array from :func:`pack_requests`) into their outputs.  C, H, W:
+    the largest channel count and image size of any request (power-of-two sizes may differ
+    between requests); returns the workspace, whose status :func:`sync_status` reads."""
     lib = _lib()
     need = lib.fdl_refocus_workspace_size(B, C, H, W)
     if ws is None or ws.numel() < need:
         ws = workspace(need, req_dev.device)
     L.check(lib.fdl_refocus(_p(req_dev), B, _p(count), C, H, W, Nmax, _p(ws), ws.numel(), _stream(stream)),
             "fdl_refocus")
+    return ws
+
+
+def sync_status(ws, stream=None) -> int:
+    """Device status word (``L.ST_*`` bits) of the last call that used workspace ``ws`` (a
+    tensor or a :class:`FitWorkspace`); synchronises the stream."""
+    buf = ws.buf if isinstance(ws, FitWorkspace) else ws
+    v = ct.c_int(0)
+    L.check(_lib().fdl_sync_status(_p(buf), ct.byref(v), _stream(stream)), "fdl_sync_status")
+    return v.value
 
 
 def aperture_table(raster: torch.Tensor, Z: int, stream=None) -> torch.Tensor:
@@ -220,12 +237,15 @@ def aperture_table(raster: torch.Tensor, Z: int, stream=None) -> torch.Tensor:
 
 
 def refocus_specs(specs: list[RenderSpec], stream=None) -> list[torch.Tensor]:
-    """Convenience: pack, render and return the output images of ``specs`` (same H, W, C)."""
+    """Convenience: pack, render and return the output images of ``specs`` in one launch
+    (image sizes may differ when they are powers of two)."""
     dev = specs[0].layers.device
     req = pack_requests(specs, dev)
-    N, C, H, Wh = specs[0].layers.shape
+    C = max(s.layers.shape[1] for s in specs)
+    H = max(s.layers.shape[2] for s in specs)
+    W = max(_width(s.layers.shape[3], s.W) for s in specs)
     Nmax = max(s.layers.shape[0] for s in specs)
-    refocus(req, len(specs), C, H, _width(Wh, specs[0].W), Nmax, stream=stream)
+    refocus(req, len(specs), C, H, W, Nmax, stream=stream)
     return [s.out for s in specs]
 
 
@@ -242,7 +262,7 @@ def pack_views(views: list, device) -> torch.Tensor:
             keep.append(pts)
         npts = 0 if pts is None else pts.shape[0]
         arr[i] = L.Request(None, None, None, pts.data_ptr() if pts is not None else None, 0, npts, L.APERTURE[kind],
-                           0.0, 0.0, float(s), float(radius), 0)
+                           0.0, 0.0, float(s), float(radius))
     return torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(device)
 
 

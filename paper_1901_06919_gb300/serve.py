@@ -3,15 +3,17 @@
 * ``FdlStore`` keeps fitted FDLs (layer spectra + disparities) on the device under
   a byte budget; admitting a new light field fits it on a side stream, evicts the
   least recently used FDLs that no in-flight request reads, and rolls back
-  cleanly if it cannot make room or the allocation fails.
-* ``Server`` groups requests by image size.  Each size class owns two batch
-  buffers, each with its own stream, device descriptor array (``fdl_request``),
-  batch-count word and workspace, and a CUDA graph that copies the descriptors
-  in and runs ``fdl_refocus`` over them.  A tick fills whichever buffer is free
-  with the queued requests (up to its capacity) and replays its graph, so
+  cleanly if it cannot make room or the allocation fails.  Each entry carries a
+  CUDA event recorded after its fit: no batch reads its layers before it.
+* ``Server`` runs a few batch buffers, each with its own stream, device
+  descriptor array (``fdl_request``), batch-count word and workspace, and a CUDA
+  graph that copies the descriptors in and runs ``fdl_refocus`` over them.  One
+  graph serves every image size: requests of different FDLs, power-of-two sizes,
+  viewpoints and apertures share a launch.  A tick fills whichever buffer is
+  free with the queued requests (up to its capacity) and replays its graph, so
   requests that arrive while a batch is on the GPU go into the next batch and
-  the two batches overlap on the device.  Completion is polled with bounded
-  waits (``TimeoutError`` past the deadline).
+  the batches overlap on the device.  Completion is polled with bounded waits
+  (``TimeoutError`` past the deadline).
 """
 
 from __future__ import annotations
@@ -44,6 +46,7 @@ class FdlEntry:
     nbytes: int
     refs: int = 0
     last_used: float = 0.0
+    ready: object = None  # CUDA event recorded after the fit (None on the CPU)
 
 
 class FdlStore:
@@ -92,11 +95,23 @@ class FdlStore:
         except (RuntimeError, MemoryError) as e:
             raise AdmissionError(f"allocation failed: {e}") from e
         dd.copy_(d)
+        ready = None
         if layers.is_cuda:
-            fdl.fit(views, u, dd, lam, eps, out=layers, stream=stream)
+            st = stream if stream is not None else torch.cuda.current_stream(layers.device)
+            # the fit (and its workspace) runs on `st`; layers and d, allocated on the current
+            # stream, are marked as used there so that the allocator keeps them until it is done
+            dd_ready = torch.cuda.Event()
+            dd_ready.record()
+            st.wait_event(dd_ready)
+            with torch.cuda.stream(st):
+                fdl.fit(views, u, dd, lam, eps, out=layers, stream=st)
+                ready = torch.cuda.Event()
+                ready.record(st)
+            layers.record_stream(st)
+            dd.record_stream(st)
         for v in victims:
             self.entries.pop(v)
-        e = FdlEntry(fid, layers, dd, H, W, C, N, need, last_used=time.perf_counter())
+        e = FdlEntry(fid, layers, dd, H, W, C, N, need, last_used=time.perf_counter(), ready=ready)
         self.entries[fid] = e
         return e
 
@@ -118,10 +133,12 @@ class Request:
     t_done: float | None = None
     out: torch.Tensor | None = None
     batch_size: int = 0
+    batch_id: int = -1  # the launch that rendered it
 
 
 class _Batch:
-    """One batch buffer of a size class: stream, descriptors, count, workspace, graph."""
+    """One batch buffer: stream, descriptors, count, workspace and the captured graph of
+    ``fdl_refocus`` over images up to (C, H, W)."""
 
     def __init__(self, H, W, C, cap, Nmax, device):
         self.H, self.W, self.C, self.cap, self.Nmax = H, W, C, cap, Nmax
@@ -155,17 +172,27 @@ class _Batch:
             self._body()
         self.stream.synchronize()
 
-    def launch(self, reqs: list[Request], store: FdlStore, pts: dict):
+    def launch(self, reqs: list[Request], store: FdlStore, pts: dict, batch_id: int = -1):
         arr = (L.Request * self.cap).from_buffer(self.host_desc.numpy())
+        waits = {}
         for i, r in enumerate(reqs):
             e = store.get(r.fid)
             p = pts.get(r.aperture)
             arr[i] = L.Request(e.layers.data_ptr(), e.d.data_ptr(), r.out.data_ptr(),
                                p.data_ptr() if p is not None else None, e.N, 0 if p is None else p.shape[0],
-                               L.APERTURE[r.aperture], float(r.u0[0]), float(r.u0[1]), float(r.s), float(r.radius), 0)
-            e.refs += 1
+                               L.APERTURE[r.aperture], float(r.u0[0]), float(r.u0[1]), float(r.s), float(r.radius),
+                               e.H, e.W, e.C)
             r.batch_size = len(reqs)
+            r.batch_id = batch_id
+            if e.ready is not None:
+                waits[e.fid] = e.ready
         self.host_count[0] = len(reqs)
+        # algorithmic bytes of the batch: each FDL's layers read once, each image written once
+        self.alg_bytes = sum(store.entries[f].nbytes for f in {r.fid for r in reqs}) + sum(
+            4 * r.out.numel() for r in reqs)
+        # a light field admitted moments ago may still be fitting on its side stream
+        for ev in waits.values():
+            self.stream.wait_event(ev)
         with torch.cuda.stream(self.stream):
             self.graph.replay()
             self.done.record(self.stream)
@@ -174,73 +201,90 @@ class _Batch:
 
 
 class Server:
-    """Continuous batching of render / refocus requests over resident FDLs."""
+    """Continuous batching of render / refocus requests over resident FDLs.
 
-    def __init__(self, store: FdlStore, sizes, Nmax: int = 64, capacity: int = 32, pool: int = 128):
+    ``sizes``: the (H, W, C) image sizes served (powers of two); one graph per batch buffer
+    covers all of them, each buffer holding up to ``capacity`` requests of any mix of sizes.
+    """
+
+    def __init__(self, store: FdlStore, sizes, Nmax: int = 64, capacity: int = 32, pool: int = 128,
+                 buffers: int = 2):
         self.store = store
         self.dev = store.device
-        self.classes = {}
-        self.pool = {}
-        for (H, W, C) in sizes:
-            self.classes[(H, W, C)] = [_Batch(H, W, C, capacity, Nmax, self.dev) for _ in range(2)]
-            self.pool[(H, W, C)] = [torch.empty((C, H, W), dtype=torch.float32, device=self.dev) for _ in range(pool)]
-        for bs in self.classes.values():
-            for b in bs:
-                b.capture()
-        self.queue: dict[tuple, collections.deque] = {k: collections.deque() for k in self.classes}
+        self.sizes = [tuple(s) for s in sizes]
+        H = max(s[0] for s in self.sizes)
+        W = max(s[1] for s in self.sizes)
+        C = max(s[2] for s in self.sizes)
+        self.batches = [_Batch(H, W, C, capacity, Nmax, self.dev) for _ in range(buffers)]
+        self.pool = {(h, w, c): [torch.empty((c, h, w), dtype=torch.float32, device=self.dev) for _ in range(pool)]
+                     for (h, w, c) in self.sizes}
+        for b in self.batches:
+            b.capture()
+        self.queue: collections.deque = collections.deque()
         self.completed: list[Request] = []
         self._fresh: list[Request] = []
         self.pts = {}
+        self.alg_bytes = 0  # algorithmic bytes of every launched batch (layers once per FDL, images)
+        self.launches = 0
 
     def submit(self, r: Request):
-        e = self.store.entries[r.fid]
-        self.queue[(e.H, e.W, e.C)].append(r)
+        # a queued request holds its FDL: admissions do not evict it before it has rendered
+        self.store.entries[r.fid].refs += 1
+        self.queue.append(r)
 
     def release(self, r: Request):
         """Return a completed request's output buffer to its pool."""
-        e_key = tuple(r.out.shape[1:]) + (r.out.shape[0],)
-        self.pool[e_key].append(r.out)
+        c, h, w = r.out.shape
+        self.pool[(h, w, c)].append(r.out)
         r.out = None
 
     def _poll(self):
         now = None
-        for bs in self.classes.values():
-            for b in bs:
-                if b.busy and b.done.query():
-                    now = now or time.perf_counter()
-                    for r in b.requests:
-                        r.t_done = now
-                        self.store.entries[r.fid].refs -= 1
-                        self.completed.append(r)
-                        self._fresh.append(r)
-                    b.requests = []
-                    b.busy = False
+        for b in self.batches:
+            if b.busy and b.done.query():
+                now = now or time.perf_counter()
+                for r in b.requests:
+                    r.t_done = now
+                    self.store.entries[r.fid].refs -= 1
+                    self.completed.append(r)
+                    self._fresh.append(r)
+                b.requests = []
+                b.busy = False
+
+    def _busy(self) -> bool:
+        return any(b.busy for b in self.batches)
 
     def tick(self) -> int:
         """Poll finished batches, then launch queued requests into free buffers; returns launches."""
         self._poll()
         launched = 0
-        for key, bs in self.classes.items():
-            q = self.queue[key]
-            for b in bs:
-                if not q:
+        for b in self.batches:
+            if not self.queue:
+                break
+            if b.busy:
+                continue
+            reqs = []
+            # FIFO; a request waits while the output pool of its size is empty
+            while self.queue and len(reqs) < b.cap:
+                r = self.queue[0]
+                e = self.store.entries[r.fid]
+                pool = self.pool[(e.H, e.W, e.C)]
+                if not pool:
                     break
-                if b.busy:
-                    continue
-                n = min(len(q), b.cap, len(self.pool[key]))
-                if n == 0:
-                    break
-                reqs = [q.popleft() for _ in range(n)]
-                for r in reqs:
-                    r.out = self.pool[key].pop()
-                b.launch(reqs, self.store, self.pts)
-                launched += 1
+                r.out = pool.pop()
+                reqs.append(self.queue.popleft())
+            if not reqs:
+                break
+            b.launch(reqs, self.store, self.pts, self.launches)
+            self.alg_bytes += b.alg_bytes
+            self.launches += 1
+            launched += 1
         return launched
 
     def drain(self, timeout_s: float = 30.0):
         """Run ticks until every queued request has completed (bounded wait)."""
         t0 = time.perf_counter()
-        while any(self.queue.values()) or any(b.busy for bs in self.classes.values() for b in bs):
+        while self.queue or self._busy():
             self.tick()
             if time.perf_counter() - t0 > timeout_s:
                 raise TimeoutError("requests did not complete within the deadline")
@@ -252,7 +296,7 @@ class Server:
         trace = sorted(trace, key=lambda r: r.t_arrival)
         for r in trace:
             r.t_arrival += t0
-        while i < len(trace) or any(self.queue.values()) or any(b.busy for bs in self.classes.values() for b in bs):
+        while i < len(trace) or self.queue or self._busy():
             now = time.perf_counter()
             while i < len(trace) and trace[i].t_arrival <= now:
                 self.submit(trace[i])

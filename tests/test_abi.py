@@ -111,7 +111,14 @@ def test_other_entry_points_reject_bad_arguments(lib):
 
 
 def test_request_struct_layout_matches_header(lib):
-    # fdl_request: 4 pointers, 3 ints, 4 floats, 1 int
-    assert ct.sizeof(L.Request) == 64
+    # fdl_request: 4 pointers, 3 ints, 4 floats, the image size (3 ints), 2 ints of padding
+    assert ct.sizeof(L.Request) == 80
     assert L.Request.u0x.offset == 44
+    assert L.Request.H.offset == 60 and L.Request.C.offset == 68
     assert ct.sizeof(L.FitOpts) == 48
+
+
+def test_status_word_call_rejects_null(lib):
+    v = ct.c_int(0)
+    assert lib.fdl_sync_status(None, ct.byref(v), None) == L.FDL_EINVAL
+    assert lib.fdl_sync_status(ct.c_void_p(0x1000), None, None) == L.FDL_EINVAL

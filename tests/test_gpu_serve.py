@@ -36,6 +36,12 @@ def test_results_are_the_same_alone_and_in_the_mix(fdl):
     stats = srv.run_trace(trace, keep_outputs=True)
     assert stats["requests"] == 60 and all(r.t_done is not None for r in trace)
     assert stats["mean_batch"] > 1.0  # requests really were batched together
+    # one graph serves every size: some launch rendered 64 x 64 and 128 x 128 images together
+    sizes_of = {}
+    for r in trace:
+        sizes_of.setdefault(r.batch_id, set()).add(store.entries[r.fid].H)
+    assert any(len(v) > 1 for v in sizes_of.values())
+    assert fdl.sync_status(srv.batches[0].ws) == 0
     for r in trace:
         e = store.entries[r.fid]
         alone = fdl.refocus_specs([fdl.RenderSpec(e.layers, e.d, r.u0, r.s, r.aperture, r.radius)])[0]

@@ -69,8 +69,8 @@ class _StuckBatch:
 
 def test_drain_times_out_on_a_batch_that_never_completes():
     srv = Server.__new__(Server)
-    srv.classes = {(16, 16, 1): [_StuckBatch()]}
-    srv.queue = {(16, 16, 1): collections.deque()}
+    srv.batches = [_StuckBatch()]
+    srv.queue = collections.deque()
     srv.completed = []
     srv._fresh = []
     srv.store = FdlStore(1 << 20, "cpu")

@@ -29,8 +29,12 @@ def test_noalloc_fit_matches_workspace_fit_twice(fdl):
 
     lib = L.load()
     stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
-    cases = [(view_grid(4), np.linspace(-3, 3, 30), 64, 3, 11), (view_grid(2), np.linspace(-2, 2, 12), 128, 1, 12)]
-    for u, d, size, C, seed in cases:
+    # (views, disparities, image size, channels, seed): FP32 + double-float tiers (N <= 32), the
+    # double-float-first path of N > 32, and an image at the size limit of the fixed scratch
+    # (1024 x 1024: 525,312 stored frequencies)
+    cases = [(view_grid(4), np.linspace(-3, 3, 30), 64, 3, 11), (view_grid(2), np.linspace(-2, 2, 12), 128, 1, 12),
+             (view_grid(2), np.linspace(-3, 3, 40), 64, 3, 13), (view_grid(1), np.linspace(-2, 2, 8), 1024, 1, 14)]
+    for i, (u, d, size, C, seed) in enumerate(cases):
         views, _ = occluding_planes(seed, size, size, C, u)
         V = torch.from_numpy(views).cuda()
         U = torch.from_numpy(u).cuda()
@@ -40,12 +44,16 @@ def test_noalloc_fit_matches_workspace_fit_twice(fdl):
         opts = L.FitOpts(1e-2, 1e-4, L.REG["view2"], L.PREC["mixed"], 0.0, 0.0)
         ref, _ = fdl.fit_spectra(S, U, D, 1e-2, 1e-4)
         out = torch.full_like(ref, float("nan"))
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         st = lib.fdl_fit_spectra_noalloc(_ptr(S), K, C, size, size, _ptr(U), _ptr(D), N, ct.byref(opts), _ptr(out),
                                          stream)
         assert st == L.FDL_OK, L.status_name(st)
         torch.cuda.synchronize()
+        if i > 0:  # after the first call (which finds the array's address): no device memory taken
+            assert torch.cuda.mem_get_info()[0] == free_before
         err = (torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref)).item()
-        assert err < TOL, err
+        assert err < TOL, (size, d.size, err)
 
 
 def test_noalloc_rejects_frequencies_beyond_its_scratch(fdl):
