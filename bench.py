@@ -446,7 +446,8 @@ def serving_leg(device, n_requests=2000, rates=(2000.0, 20000.0), budget=2.5e9, 
                 except Exception:  # every resident FDL in use: no room this time
                     pass
                 next_fid[0] += 1
-            live = list(store.entries)
+            # requests go to light fields whose fit has finished (a new one is still fitting)
+            live = [f for f, e in store.entries.items() if e.ready is None or e.ready.query()]
             r.fid = live[int(picks[r.rid]) % len(live)]
             orig_submit(r)
 
@@ -898,7 +899,12 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the 1024x1024 precision leg")
     ap.add_argument("--no-shapes", action="store_true", help="skip the leg at the paper's non-power-of-two sizes")
     ap.add_argument("--no-calib", action="store_true", help="skip the calibration leg")
+    ap.add_argument("--case", default=None, choices=sorted(CASES),
+                    help="run one bounded case twice and exit (for profiler captures)")
     args = ap.parse_args()
+    if args.case:
+        CASES[args.case]()
+        return
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -1053,6 +1059,71 @@ FP32_METHOD_FLOPS_PER_FREQUENCY = 145_000
 # of the current kernel (None: not captured since it last changed).  The algorithmic bytes are
 # the K x C spectrum values read and the N x C layer values written, 8 bytes each: 2,664.
 DF_DRAM_BYTES_PER_FREQUENCY = None
+
+
+# ------------------------------------------------------------------ bounded cases for profilers
+def _case_device():
+    import torch
+
+    from paper_1901_06919_gb300 import build as B
+
+    B.build()
+    return torch, torch.device("cuda", 0)
+
+
+def case_df512():
+    """The double-float solve of every frequency of the 9x9-view 512x512 RGB workload, twice."""
+    torch, dev = _case_device()
+    import paper_1901_06919_gb300 as F
+
+    views, u, d, _ = workload_inputs()
+    S = F.rfft2(torch.from_numpy(views).to(dev))
+    U, D = torch.from_numpy(u).to(dev), torch.from_numpy(d).to(dev)
+    for _ in range(2):
+        x, ws = F.fit_spectra(S, U, D, LAM, EPS, precision="df")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "df512", "tiers": ws.tier_counts()}))
+
+
+def case_render81():
+    """fdl_render of the 81 input views from the layers of the 9x9-view workload, twice."""
+    torch, dev = _case_device()
+    import paper_1901_06919_gb300 as F
+
+    views, u, d, _ = workload_inputs()
+    U, D = torch.from_numpy(u).to(dev), torch.from_numpy(d).to(dev)
+    x, _ = F.fit(torch.from_numpy(views).to(dev), U, D, LAM, EPS)
+    for _ in range(2):
+        img = F.render(x, D, U)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "render81", "shape": list(img.shape)}))
+
+
+def case_fused_mixed():
+    """One fdl_refocus launch over 24 requests of three FDLs of 256^2, 512^2 and 1024^2 RGB
+    (N = 16, 30, 40; views, discs and squares), twice: the fused render path."""
+    torch, dev = _case_device()
+    import paper_1901_06919_gb300 as F
+    from scenes import random_layer_spectra
+
+    rng = np.random.default_rng(0)
+    fdls = []
+    for i, (n, Nl) in enumerate(((256, 16), (512, 30), (1024, 40))):
+        X = torch.from_numpy(random_layer_spectra(i, Nl, 3, n, n)).to(dev)
+        fdls.append((X, torch.linspace(-3, 3, Nl, device=dev)))
+    specs = []
+    for i in range(24):
+        X, dd = fdls[i % 3]
+        kind = ("pinhole", "disc", "square")[i % 3]
+        specs.append(F.RenderSpec(X, dd, tuple(rng.uniform(-4, 4, 2)), float(rng.uniform(-3, 3)), kind,
+                                  0.0 if kind == "pinhole" else float(rng.uniform(0.5, 3))))
+    for _ in range(2):
+        F.refocus_specs(specs)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "fused_mixed", "requests": len(specs)}))
+
+
+CASES = {"df512": case_df512, "render81": case_render81, "fused_mixed": case_fused_mixed}
 
 
 def measured_hbm():
