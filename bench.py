@@ -173,30 +173,37 @@ def time_device_steps(path, steps, warmup):
 
 
 def time_e2e(path, views_host, steps, warmup):
-    """Views from pinned host memory -> fit -> 81 + 32 images back to pinned host memory, through
-    the package's host pipeline (the copies of one step overlap the computation of the steps
-    beside it).  Device span from the first copy-in to the last copy-out, CUDA events."""
+    """Views from pinned host memory -> fit -> 81 + 32 images back to pinned host memory, each
+    step one call of the C ABI's fdl_fit_render_host (copies, fit and render enqueued by the
+    library) on one of two streams, so that the copies of one step overlap the computation of
+    the next.  Device span from the first copy-in to the last copy-out, CUDA events."""
     torch = path.torch
     from paper_1901_06919_gb300.pipeline import FitRenderPipeline
 
     refocus = [((0.0, 0.0), float(s), "disc", 1.0) for s in path.s_list]
     pipe = FitRenderPipeline(len(path.u), C, H, W, path.u, path.d, LAM, EPS, u0=path.u0, refocus=refocus,
                              device=path.dev)
-    out_host = torch.empty((len(path.u0) + len(refocus), C, H, W), dtype=torch.float32).pin_memory()
-    for _ in range(warmup):
-        pipe.submit(views_host, out_host)
+    out_host = [torch.empty((len(path.u0) + len(refocus), C, H, W), dtype=torch.float32).pin_memory()
+                for _ in range(2)]
+    for i in range(warmup):
+        pipe.submit(views_host, out_host[i % 2])
     pipe.wait()
     torch.cuda.synchronize()
+    s0, s1 = pipe.slots[0]["stream"], pipe.slots[1]["stream"]
     a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(pipe.s_in)
-    for _ in range(steps):
-        pipe.submit(views_host, out_host)
-    b.record(pipe.s_out)
+    a.record(s0)
+    s1.wait_event(a)
+    n0 = pipe.n
+    for i in range(steps):
+        pipe.submit(views_host, out_host[(n0 + i) % 2])
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record(s0)
+    b1.record(s1)
     pipe.wait()
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / steps
-    return ms, views_host.numel() * 4, out_host.numel() * 4
+    ms = max(a.elapsed_time(b0), a.elapsed_time(b1)) / steps
+    return ms, views_host.numel() * 4, out_host[0].numel() * 4
 
 
 def time_kernel_legs(path, reps=10):
@@ -966,7 +973,8 @@ def main():
         "latency": {"render_p50_ms": p50, "render_p99_ms": p99, "requests": 64, "mode": "one at a time"},
         "e2e": {"value": world * q_half() / (e2e_ms / 1e3) / 1e6, "unit": "Mfreq/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": "pipeline.FitRenderPipeline (copy-in, compute and copy-out streams, two slots)"},
+                "api": "fdl_fit_render_host (C ABI: views from pinned host memory, fit, 113 renders, images back to "
+                       "pinned host memory), alternating two streams and two device slots"},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
         "roofline": rl,
@@ -1123,7 +1131,18 @@ def case_fused_mixed():
     print(json.dumps({"case": "fused_mixed", "requests": len(specs)}))
 
 
-CASES = {"df512": case_df512, "render81": case_render81, "fused_mixed": case_fused_mixed}
+def case_step():
+    """Three warm-up steps and two steps of the benchmark (fit + 81 views + 32 refocused images)."""
+    torch, dev = _case_device()
+    views, u, d, s_list = workload_inputs()
+    path = FdlPath(dev, views, u, d, s_list)
+    for _ in range(5):
+        path.step()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "step", "tiers": path.F.FitWorkspace.tier_counts(path.ws_fit)}))
+
+
+CASES = {"df512": case_df512, "render81": case_render81, "fused_mixed": case_fused_mixed, "step": case_step}
 
 
 def measured_hbm():

@@ -232,13 +232,32 @@ FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H,
  * rendered by Eq. BsFourier straight into the inverse column DFT (the
  * rendered spectrum is never written to memory), then the inverse row DFT
  * writes its output.  Otherwise (sizes that are not powers of two, or
- * H = 4096) every request must have exactly H x W x C.  If count is not NULL
+ * H = 4096), and for a single request (B = 1), every request must have
+ * exactly H x W x C.  If count is not NULL
  * it is a DEVICE int: only requests [0, *count) are rendered, so that a
  * captured CUDA graph can be replayed with a varying batch.  Nmax <= 64. */
 FDL_API size_t fdl_refocus_workspace_size(int B, int C, int H, int W);
 FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, int H,
                         int W, int Nmax, void* workspace, size_t workspace_bytes,
                         void* stream);
+
+/* One light field from host memory to host memory: the views (HOST
+ * float32 [K][C][H][W]) are read by the forward DFT where they are when they
+ * are pinned (mapped into the device's address space; NVLink-C2C on GB300),
+ * else copied into the workspace first; fitted into `layers` (DEVICE
+ * [N][C][H][W/2+1]) as by
+ * fdl_fit, the B requests (DEVICE array, as for fdl_refocus with bounds C, H,
+ * W and Nmax = N; they read `layers` and write inside `images`) are rendered,
+ * and `images` (DEVICE, image_floats floats) is copied to images_host (HOST,
+ * pinned).  Everything is enqueued on `stream`; callers overlap the copies of
+ * one light field with the computation of another by alternating two streams
+ * and two sets of buffers.  Workspace: fdl_fit_render_host_workspace_size. */
+FDL_API size_t fdl_fit_render_host_workspace_size(int K, int C, int H, int W, int N, int B);
+FDL_API int fdl_fit_render_host(const float* views_host, int K, int C, int H, int W, const float* u,
+                                const float* d, int N, const fdl_fit_opts* opts, float* layers,
+                                const fdl_request* req, int B, float* images, size_t image_floats,
+                                float* images_host, void* workspace, size_t workspace_bytes,
+                                void* stream);
 
 /* Table of a drawn aperture (Sec. VI-A: the aperture is drawn, zero-padded
  * and transformed, and psi_hat is linearly interpolated).  raster: DEVICE

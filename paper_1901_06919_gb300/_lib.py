@@ -68,6 +68,10 @@ _SIGS = [
                                            ct.c_void_p, ct.c_int, ct.POINTER(FitOpts), ct.c_void_p, ct.c_void_p]),
     ("fdl_fit_tier_counts", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.c_void_p]),
     ("fdl_sync_status", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int), ct.c_void_p]),
+    ("fdl_fit_render_host_workspace_size", ct.c_size_t, [ct.c_int] * 6),
+    ("fdl_fit_render_host", ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                       ct.c_int, ct.POINTER(FitOpts), ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p,
+                                       ct.c_size_t, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p]),
     ("fdl_render_workspace_size", ct.c_size_t, [ct.c_int] * 4),
     ("fdl_render", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
                               ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p]),

@@ -502,8 +502,56 @@ FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const RenderWs w = carve_render(workspace, B, C, H, W, false);
   cudaError_t e = cudaMemsetAsync(w.header, 0, kHeaderInts * sizeof(int), st);
-  if (e == cudaSuccess) e = render_requests(req, B, count, C, H, W, Nmax, w, st, true);
+  // one request reads one FDL: the tiled path, without the device check (if its size is not
+  // exactly (C, H, W) the kernels reject it)
+  if (e == cudaSuccess) e = render_requests(req, B, count, C, H, W, Nmax, w, st, B > 1);
   return cuda_status(e);
+}
+
+// ------------------------------------------------------------------ host buffers
+FDL_API size_t fdl_fit_render_host_workspace_size(int K, int C, int H, int W, int N, int B) {
+  const size_t fit = fdl_fit_workspace_size(K, C, H, W, N);
+  const size_t ren = fdl_refocus_workspace_size(B, C, H, W);
+  if (fit == 0 || ren == 0) return 0;
+  return align_up((size_t)K * C * H * W * sizeof(float)) + align_up(fit) + ren;
+}
+
+FDL_API int fdl_fit_render_host(const float* views_host, int K, int C, int H, int W, const float* u, const float* d,
+                                int N, const fdl_fit_opts* opts, float* layers, const fdl_request* req, int B,
+                                float* images, size_t image_floats, float* images_host, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+  int s = check_fit_args(K, C, H, W, N, opts);
+  if (s != FDL_OK) return s;
+  if (B < 1 || !views_host || !u || !d || !layers || !req || !images || !images_host || !workspace) return FDL_EINVAL;
+  if (workspace_bytes < fdl_fit_render_host_workspace_size(K, C, H, W, N, B)) return FDL_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(workspace);
+  float* staging = reinterpret_cast<float*>(base);
+  void* ws_fit = base + align_up((size_t)K * C * H * W * sizeof(float));
+  const size_t fit_bytes = align_up(fdl_fit_workspace_size(K, C, H, W, N));
+  void* ws_ren = static_cast<char*>(ws_fit) + fit_bytes;
+  // Pinned host memory is mapped into the device's address space (NVLink-C2C on GB300): the
+  // forward DFT then reads the views where they are; other memory is staged by a copy.
+  const float* views = nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, views_host) == cudaSuccess) {
+    if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) views = static_cast<const float*>(at.devicePointer);
+  } else {
+    cudaGetLastError();  // clear the error of an unknown pointer
+  }
+  if (views == nullptr) {
+    if (cudaMemcpyAsync(staging, views_host, (size_t)K * C * H * W * sizeof(float), cudaMemcpyDefault, st) !=
+        cudaSuccess)
+      return FDL_ECUDA;
+    views = staging;
+  }
+  s = fdl_fit(views, K, C, H, W, u, d, N, opts, layers, ws_fit, fit_bytes, stream);
+  if (s != FDL_OK) return s;
+  s = fdl_refocus(req, B, nullptr, C, H, W, N, ws_ren, fdl_refocus_workspace_size(B, C, H, W), stream);
+  if (s != FDL_OK) return s;
+  if (cudaMemcpyAsync(images_host, images, image_floats * sizeof(float), cudaMemcpyDefault, st) != cudaSuccess)
+    return FDL_ECUDA;
+  return FDL_OK;
 }
 
 // ------------------------------------------------------------------ device status

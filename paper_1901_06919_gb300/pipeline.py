@@ -1,22 +1,18 @@
 """Host-to-host pipeline over a sequence of light fields: views in pinned host memory ->
 layers (Sec. V-A) -> rendered views and refocused images (Sec. VI-A) back in pinned host
-memory, with the copies of one light field overlapping the computation of its neighbours.
+memory, through the C ABI's ``fdl_fit_render_host`` (the library enqueues the copies, the
+fit and the render).
 
-Two device slots and three streams:
-
-* copy-in: the views of submission i into slot i % 2, once the fit of submission i - 2 has
-  finished reading that slot;
-* compute: ``fdl_fit``, ``fdl_render`` and ``fdl_refocus`` of the slot, once its views are in
-  and the copy-out of submission i - 2 has finished reading the slot's images;
-* copy-out: the slot's images, one contiguous ``[B + R][C][H][W]`` block, to the caller's
-  pinned buffer.
-
-All ordering is by CUDA events; the host waits only in :meth:`FitRenderPipeline.wait`.  The
-caller keeps each submission's host buffers alive and unmodified until it has been waited for.
+Two slots, each with its own stream, layers, device images, request descriptors and
+workspace; submission i goes to slot i % 2, so that the copies of one light field overlap
+the computation of its neighbour on the other stream.  The host waits only in
+:meth:`FitRenderPipeline.wait`.  The caller keeps each submission's host buffers alive and
+unmodified until it has been waited for.
 """
 
 from __future__ import annotations
 
+import ctypes as ct
 import time
 
 import torch
@@ -47,21 +43,21 @@ class FitRenderPipeline:
         lib = L.load()
         self.slots = []
         for _ in range(2):
-            s = {"views": torch.empty((K, C, H, W), dtype=torch.float32, device=self.dev),
-                 "layers": torch.empty((self.N, C, H, W // 2 + 1), dtype=torch.complex64, device=self.dev),
-                 "out": torch.empty((self.B + self.R, C, H, W), dtype=torch.float32, device=self.dev),
-                 "ws_fit": fdl.FitWorkspace(fdl.workspace(lib.fdl_fit_workspace_size(K, C, H, W, self.N), self.dev)),
-                 "ws_render": fdl.workspace(lib.fdl_render_workspace_size(max(self.B, 1), C, H, W), self.dev),
-                 "ws_refocus": fdl.workspace(lib.fdl_refocus_workspace_size(max(self.R, 1), C, H, W), self.dev),
-                 "views_read": None, "out_read": None, "done": None}
-            if self.R:
-                specs = [fdl.RenderSpec(s["layers"], self.d, tuple(map(float, r[0])), float(r[1]), r[2], float(r[3]),
-                                        out=s["out"][self.B + i]) for i, r in enumerate(refocus)]
-                s["req"] = fdl.pack_requests(specs, self.dev)
-            self.slots.append(s)
-        self.s_in = torch.cuda.Stream(self.dev)
-        self.s_comp = torch.cuda.Stream(self.dev)
-        self.s_out = torch.cuda.Stream(self.dev)
+            sl = {"layers": torch.empty((self.N, C, H, W // 2 + 1), dtype=torch.complex64, device=self.dev),
+                  "out": torch.empty((self.B + self.R, C, H, W), dtype=torch.float32, device=self.dev),
+                  "ws": fdl.workspace(lib.fdl_fit_render_host_workspace_size(K, C, H, W, self.N, self.B + self.R),
+                                      self.dev),
+                  "stream": torch.cuda.Stream(self.dev)}
+            specs = [fdl.RenderSpec(sl["layers"], self.d, tuple(map(float, self.u0[b].tolist())), out=sl["out"][b])
+                     for b in range(self.B)]
+            specs += [fdl.RenderSpec(sl["layers"], self.d, tuple(map(float, r[0])), float(r[1]), r[2], float(r[3]),
+                                     out=sl["out"][self.B + i]) for i, r in enumerate(refocus)]
+            if not specs:
+                raise ValueError("nothing to render: give u0 or refocus")
+            sl["req"] = fdl.pack_requests(specs, self.dev)
+            self.slots.append(sl)
+        self.opts = fdl._opts(self.lam, self.eps, reg, precision, 0.0)
+        torch.cuda.synchronize(self.dev)  # descriptors in place before the slot streams read them
         self.n = 0
         self.pending: dict[int, torch.cuda.Event] = {}
 
@@ -72,36 +68,17 @@ class FitRenderPipeline:
             raise ValueError("views_host must be float32 [K][C][H][W]")
         if tuple(out_host.shape) != (self.B + self.R, self.C, self.H, self.W) or out_host.dtype != torch.float32:
             raise ValueError("out_host must be float32 [B + R][C][H][W]")
-        s = self.slots[self.n % 2]
-        ev_in = torch.cuda.Event()
-        with torch.cuda.stream(self.s_in):
-            if s["views_read"] is not None:
-                self.s_in.wait_event(s["views_read"])
-            s["views"].copy_(views_host, non_blocking=True)
-            ev_in.record(self.s_in)
-        with torch.cuda.stream(self.s_comp):
-            self.s_comp.wait_event(ev_in)
-            fdl.fit(s["views"], self.u, self.d, self.lam, self.eps, reg=self.reg, precision=self.precision,
-                    out=s["layers"], ws=s["ws_fit"], stream=self.s_comp)
-            s["views_read"] = torch.cuda.Event()
-            s["views_read"].record(self.s_comp)
-            if s["out_read"] is not None:
-                self.s_comp.wait_event(s["out_read"])
-            if self.B:
-                fdl.render(s["layers"], self.d, self.u0, out=s["out"][:self.B], ws=s["ws_render"], stream=self.s_comp)
-            if self.R:
-                fdl.refocus(s["req"], self.R, self.C, self.H, self.W, self.N, ws=s["ws_refocus"], stream=self.s_comp)
-            ev_comp = torch.cuda.Event()
-            ev_comp.record(self.s_comp)
-        with torch.cuda.stream(self.s_out):
-            self.s_out.wait_event(ev_comp)
-            out_host.copy_(s["out"], non_blocking=True)
-            s["out_read"] = torch.cuda.Event()
-            s["out_read"].record(self.s_out)
-        # every stream that touched caller memory has to finish before the ticket completes
+        if views_host.is_cuda or out_host.is_cuda or not views_host.is_contiguous() or not out_host.is_contiguous():
+            raise ValueError("views_host and out_host must be contiguous host tensors")
+        sl = self.slots[self.n % 2]
+        st = sl["stream"]
+        L.check(L.load().fdl_fit_render_host(
+            views_host.data_ptr(), self.K, self.C, self.H, self.W, self.u.data_ptr(), self.d.data_ptr(), self.N,
+            ct.byref(self.opts), sl["layers"].data_ptr(), sl["req"].data_ptr(), self.B + self.R,
+            sl["out"].data_ptr(), sl["out"].numel(), out_host.data_ptr(), sl["ws"].data_ptr(), sl["ws"].numel(),
+            ct.c_void_p(st.cuda_stream)), "fdl_fit_render_host")
         done = torch.cuda.Event()
-        self.s_out.wait_event(ev_in)
-        done.record(self.s_out)
+        done.record(st)
         ticket = self.n
         self.pending[ticket] = done
         self.n += 1

@@ -173,6 +173,9 @@ class _Batch:
         self.stream.synchronize()
 
     def launch(self, reqs: list[Request], store: FdlStore, pts: dict, batch_id: int = -1):
+        # requests of one FDL side by side: the fused render's consecutive CTAs then read the
+        # same strip of layer values, which stays in L2 between them
+        reqs = sorted(reqs, key=lambda r: r.fid)
         arr = (L.Request * self.cap).from_buffer(self.host_desc.numpy())
         waits = {}
         for i, r in enumerate(reqs):

@@ -118,6 +118,17 @@ def test_request_struct_layout_matches_header(lib):
     assert ct.sizeof(L.FitOpts) == 48
 
 
+def test_host_buffer_step_rejects_bad_arguments(lib):
+    p = ct.c_void_p(0x1000)
+    o = _opts()
+    assert lib.fdl_fit_render_host_workspace_size(9, 1, 64, 64, 8, 4) > 9 * 64 * 64 * 4
+    call = lambda B=4, views=p, ws=1 << 40: lib.fdl_fit_render_host(views, 9, 1, 64, 64, p, p, 8, ct.byref(o), p, p, B,
+                                                                   p, 10, p, p, ws, None)
+    assert call(B=0) == L.FDL_EINVAL
+    assert call(views=ct.c_void_p(0)) == L.FDL_EINVAL
+    assert call(ws=64) == L.FDL_ENOMEM
+
+
 def test_status_word_call_rejects_null(lib):
     v = ct.c_int(0)
     assert lib.fdl_sync_status(None, ct.byref(v), None) == L.FDL_EINVAL

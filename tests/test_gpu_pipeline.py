@@ -1,5 +1,5 @@
-"""The host pipeline (copy-in, compute, copy-out streams over two device slots) returns, for
-every submission, exactly what the step-by-step calls return for the same light field."""
+"""The host pipeline (fdl_fit_render_host on two streams and two device slots) returns, for
+every submission, what the step-by-step calls return for the same light field."""
 
 import numpy as np
 import pytest
@@ -31,7 +31,8 @@ def test_pipeline_matches_sequential_calls(fdl):
         specs = [fdl.RenderSpec(x, d.cuda(), r[0], r[1], r[2], r[3]) for r in refocus]
         ref.append(torch.stack(fdl.refocus_specs(specs)))
         ref = torch.cat(ref).cpu()
-        assert torch.equal(o, ref)
+        # one refocus launch over all the images sums the layers in its own order
+        assert torch.max(torch.abs(o - ref)).item() < 1e-5
 
 
 def test_pipeline_rejects_wrong_shapes(fdl):
