@@ -949,10 +949,12 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, device)
     legs = time_kernel_legs(path)
     p50, p99 = time_latency(path)
-    # kernels per step: fit = twiddle table + rows + cols + exp table + moment check + FP32 solve
-    # + 3 selection + 2 double-float solves (one exits at once) + 3 selection + FP64 solve + status;
-    # render = requests + 2 fused render/column passes + rows; refocus = 2 fused passes + rows
-    launches = 16 + 4 + 3
+    # kernels per step (the ncu launch list of --case step): fit = 2 twiddle tables + rows +
+    # cols + exp table + moment check + FP32 solve + 3 selection + 2 double-float solves (one
+    # exits at once) + 3 selection + FP64 solve + status = 16; fdl_render = requests + render +
+    # column and row passes = 4; fdl_refocus = gate + 3 fused launches (return at once) +
+    # render + column and row passes = 7
+    launches = 16 + 4 + 7
 
     fit_ms = stages["fit_ms"]
     render_ms = stages["render81_ms"] + stages["refocus32_ms"]
@@ -1064,9 +1066,10 @@ def moment_form_applies(u, d):
 FP32_METHOD_FLOPS_PER_FREQUENCY = 145_000
 
 # DRAM bytes (read + write) per frequency of k_solve_df<30, 15, moment form> from an ncu capture
-# of the current kernel (None: not captured since it last changed).  The algorithmic bytes are
-# the K x C spectrum values read and the N x C layer values written, 8 bytes each: 2,664.
-DF_DRAM_BYTES_PER_FREQUENCY = None
+# of the all-frequency launch (bench.py --case df512: 271.07 MB read, 79.06 MB written).  The
+# algorithmic bytes are the K x C spectrum values read and the N x C layer values written,
+# 8 bytes each: 2,664.
+DF_DRAM_BYTES_PER_FREQUENCY = (271.074304e6 + 79.06048e6) / 131_584
 
 
 # ------------------------------------------------------------------ bounded cases for profilers
@@ -1199,8 +1202,9 @@ def stage_rooflines(legs):
                          layers + N_REFOCUS * img, legs["refocus32_ms"], None)]
 
 
-# DRAM bytes (read + write) per launch from ncu captures of the current kernels (None: not captured).
-DFT_DRAM_BYTES = None
+# DRAM bytes (read + write) per launch from ncu captures of the current kernels (None: not
+# captured): the forward DFT's two passes from bench.py --case render81.
+DFT_DRAM_BYTES = (254.834944e6 + 209.893632e6) + (254.8416e6 + 201.214976e6)
 RENDER81_DRAM_BYTES = None
 
 
