@@ -60,7 +60,8 @@ struct SolveParams {
   float* err;          // per bin: condition estimate x |x| of the last pass (nullable)
   float* xn2;          // per bin: |x|^2 of the last pass that solved it
   int* counters;       // [0] FP32 bins, [1] double-float bins, [2] breakdowns, [3] non-finite,
-                       // [4] double-float list length, [5] FP64 list length, [6] FP64 bins
+                       // [4] double-float list length, [5] FP64 list length, [6] FP64 bins,
+                       // [8] moment form applies, [10] views on the integer lattice
   const float4* exp_table;  // df table of exp(2 pi i n / 1024), n in [0, 1024)
   const float* P = nullptr;               // free shifts [K][N][2] (k_solve_hp only)
   const fdl_request* views = nullptr;     // per-image apertures [K] (k_solve_hp only)
@@ -150,6 +151,9 @@ __device__ __forceinline__ bool request_ok(const fdl_request& r, int C, int H, i
 // Every workspace starts with kHeaderInts ints: the counters of a fit and, at index
 // kStatusWord, the device status word (FDL_ST_* bits) that fdl_sync_status reads.
 constexpr int kHeaderInts = 16;
+// Views on an integer lattice |u_x|, |u_y| <= kLatMax (counters[10], set by k_mom_check) let the
+// solves form A_jk = P_k^{u_x} Q_k^{u_y} from per-frequency powers.
+constexpr int kLatMax = 4;
 constexpr int kStatusWord = 15;
 constexpr int kGateWord = 14;  // renders: 1 = the tiled path serves the batch, 0 = the fused path
 

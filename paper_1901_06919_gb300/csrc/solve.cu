@@ -8,7 +8,16 @@
 //
 // Two kernels:
 //  * k_solve_f32: FP32, one warp per frequency, lane i owns row i of the
-//    Hermitian matrix in registers.  With estimate set it also records, per
+//    Hermitian matrix in registers.  Where the moment form applies (the
+//    disparities lie on a grid d_k = d_0 + k Delta + e_k with small e_k; the flag
+//    k_mom_check sets) the Gram matrix is assembled from N sums per view instead of
+//    N^2: G_rl = sum_j conj(A_jr) A_jl = W_0(m) + 2 pi i eta W_1(m) for l >= r,
+//    m = l - r, eta = e_l - e_r - e_m, W_s(m) = sum_j theta_j^s conj(A_j0) A_jm,
+//    theta_j = u_j . w (the exponential of the small phase 2 pi eta theta_j to
+//    first order; the flag bounds it by 1e-4, whose square is below FP32
+//    rounding), and G_rl = conj(G_lr) below the diagonal.  On an integer view
+//    lattice A_jr = P_r^a Q_r^b from per-frequency powers P_r^k = exp(2 pi i k d_r w_x),
+//    Q_r^k = exp(2 pi i k d_r w_y).  With estimate set it also records, per
 //    frequency, an error scale kappa |x| (kappa from three steps of power
 //    iteration for the largest eigenvalue and three steps of inverse
 //    iteration with the factor for the smallest; +inf where the factorisation
@@ -27,7 +36,8 @@ constexpr int kViewChunk = 32;  // views staged per pass
 
 // ------------------------------------------------------------------ FP32
 template <int NMAX>
-__global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int estimate) {
+// two CTAs per SM: the register allocation must stay within 128 per thread
+__global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, int estimate) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -45,6 +55,12 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
   const int Qs = p.H * (M + 1);
   const int ntiles = (Qs + kTileBins - 1) / kTileBins;  // the last tile may be partial
   const float dl = lane < N ? __ldg(p.d + lane) : 0.f;
+  // moment form and view lattice (k_mom_check's flags; warp-uniform)
+  const bool mom = p.mom != nullptr && NMAX <= 32 && *((volatile int*)(p.counters + 8)) == 1;
+  // (the powers take 2 kLatMax x 32 words of the warp's factor storage)
+  const bool lat = mom && NMAX * (NMAX + 1) >= 2 * kLatMax * 32 && *((volatile int*)(p.counters + 10)) == 1;
+  const float el = (mom && lane < N) ? p.mom[lane].x : 0.f;  // e_lane
+  float2* ptab = myL;  // lattice powers [2 kLatMax][32] while the Gram matrix is built
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // warps past the last bin of a partial tile solve the last bin again (every warp
@@ -62,6 +78,22 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
     float2 y[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) y[c] = make_float2(0.f, 0.f);
+    float2 W0 = make_float2(0.f, 0.f), W1 = make_float2(0.f, 0.f);  // moment sums, m = lane
+    if (lat) {
+      // P^k, Q^k of this lane's row; only this lane reads them back (the barrier orders
+      // the writes after the previous frequency's reads of the factor in the same words)
+      __syncwarp();
+      if (lane < N) {
+#pragma unroll 1
+        for (int k = 1; k <= kLatMax; ++k) {
+          float2 t;
+          sincospif(2.f * phase_cycles((float)k, 0.f, fq, dl), &t.y, &t.x);
+          ptab[(k - 1) * 32 + lane] = t;
+          sincospif(2.f * phase_cycles(0.f, (float)k, fq, dl), &t.y, &t.x);
+          ptab[(kLatMax + k - 1) * 32 + lane] = t;
+        }
+      }
+    }
     for (int j0 = 0; j0 < K; j0 += kViewChunk) {
       const int nv = min(kViewChunk, K - j0);
       __syncthreads();
@@ -78,8 +110,36 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
         const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
         float2 a = make_float2(0.f, 0.f);
         if (lane < N) {
-          const float f = phase_cycles(uj.x, uj.y, fq, dl);
-          sincospif(2.f * f, &a.y, &a.x);
+          if (lat) {
+            // A_jr = P_r^a Q_r^b, conjugates for negative powers
+            const int ax = (int)uj.x, by = (int)uj.y;
+            float2 pa = make_float2(1.f, 0.f), qb = make_float2(1.f, 0.f);
+            if (ax != 0) pa = ptab[(abs(ax) - 1) * 32 + lane];
+            if (by != 0) qb = ptab[(kLatMax + abs(by) - 1) * 32 + lane];
+            if (ax < 0) pa.y = -pa.y;
+            if (by < 0) qb.y = -qb.y;
+            a = cmul(pa, qb);
+          } else {
+            const float f = phase_cycles(uj.x, uj.y, fq, dl);
+            sincospif(2.f * f, &a.y, &a.x);
+          }
+        }
+        if (mom) {
+          // w_jm = conj(A_j0) A_jm in lane m: W_0 += w, W_1 += theta_j w
+          const float2 a0 = make_float2(__shfl_sync(0xffffffffu, a.x, 0), __shfl_sync(0xffffffffu, a.y, 0));
+          const float2 w = cmulc(a0, a);
+          const float th = fmaf(uj.x, wx, uj.y * wy);
+          W0.x += w.x;
+          W0.y += w.y;
+          W1.x = fmaf(th, w.x, W1.x);
+          W1.y = fmaf(th, w.y, W1.y);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (c < C) {
+              cfmac(y[c], a, bstage[(jj * C + c) * kTileBins + warp]);
+            }
+          }
+          continue;
         }
         if (lane < NMAX) myA[lane] = a;
         __syncwarp();
@@ -100,6 +160,21 @@ __global__ void __launch_bounds__(kTileBins * 32) k_solve_f32(SolveParams p, int
       }
     }
 
+    if (mom) {
+      // G_rl from the moment sums of lane m = |l - r|
+#pragma unroll
+      for (int l = 0; l < NMAX; ++l) {
+        const bool up = l >= lane;
+        const int m = up ? l - lane : lane - l;
+        const float2 w0 = make_float2(__shfl_sync(0xffffffffu, W0.x, m), __shfl_sync(0xffffffffu, W0.y, m));
+        const float2 w1 = make_float2(__shfl_sync(0xffffffffu, W1.x, m), __shfl_sync(0xffffffffu, W1.y, m));
+        const float em = __shfl_sync(0xffffffffu, el, m), ell = __shfl_sync(0xffffffffu, el, l);
+        const float t = 6.2831853f * ((up ? ell - el : el - ell) - em);
+        float2 g = make_float2(fmaf(-t, w1.y, w0.x), fmaf(t, w1.x, w0.y));
+        if (!up) g.y = -g.y;
+        G[l] = (l < N && lane < N) ? g : make_float2(0.f, 0.f);
+      }
+    }
     // an input that is not finite reaches every right-hand side (|A_jk| = 1): lane 0's
     // row is checked
     bool finite = true;

@@ -45,11 +45,16 @@ constexpr int kDfWarps = 4;
 // N = 30: 23.6 / 19.7 / 23.6 ms; N = 40: 41.5 / 66.3 / 69.5 ms, where spills dominate).
 constexpr int df_min_blocks(int nmax) { return nmax <= 16 ? 4 : (nmax <= 32 ? 3 : 2); }
 
+// Views on an integer lattice u_j = (a_j, b_j), |a_j|, |b_j| <= kLatMax: A_jr = P_r^a Q_r^b with
+// P_r^k = exp(2 pi i k d_r w_x), Q_r^k = exp(2 pi i k d_r w_y), formed once per frequency.
+__host__ __device__ constexpr int df_lat_f4(int nmax) { return nmax <= 40 ? 2 * kLatMax * 32 * ((nmax + 31) / 32) : 0; }
+
 // float4 words of shared memory per warp: A_j / next pivot column and the current column
 // (NMAX + 1 each), the packed factor, [NMAX][4] right-hand sides, 2 x 4 pivot-row values,
-// NMAX double-float reciprocals, 3 x 32 view-only values of a chunk of views (moment form)
+// NMAX double-float reciprocals, 3 x 32 view-only values of a chunk of views (moment form),
+// the lattice powers [2 kLatMax][32 R] (N <= 40)
 __host__ __device__ constexpr int df_warp_f4(int nmax) {
-  return 2 * (nmax + 1) + nmax * (nmax + 1) / 2 + 4 * nmax + 8 + (nmax + 1) / 2 + 96;
+  return 2 * (nmax + 1) + nmax * (nmax + 1) / 2 + 4 * nmax + 8 + (nmax + 1) / 2 + 96 + df_lat_f4(nmax);
 }
 
 // entry (r, l), l <= r, numbered column-major: column l starts at l*N - l(l-1)/2
@@ -190,11 +195,14 @@ __global__ void k_mom_check(const float* __restrict__ d, int N, const float* __r
     emax = fmaxf(emax, e.hi);
   }
   float umax = 0.f;
+  bool lattice = true;
   for (int j = lane; j < K; j += 32) {
     const float ux = u[2 * j], uy = u[2 * j + 1];
     finite = finite && isfinite(ux) && isfinite(uy);
     umax = fmaxf(umax, sqrtf(ux * ux + uy * uy));
+    lattice = lattice && ux == rintf(ux) && uy == rintf(uy) && fabsf(ux) <= (float)kLatMax && fabsf(uy) <= (float)kLatMax;
   }
+  lattice = __all_sync(0xffffffffu, lattice);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
@@ -206,6 +214,7 @@ __global__ void k_mom_check(const float* __restrict__ d, int N, const float* __r
     // relative slack for the low words of e, which max/min of the high words ignore
     const float x = 6.2831853f * (emax - emin) * 1.0001f * umax * 0.70710678f + 1e-30f;
     counters[8] = (all_finite && N <= 64 && x <= kMomXLim) ? 1 : 0;
+    counters[10] = (all_finite && lattice) ? 1 : 0;
   }
 }
 
@@ -244,6 +253,9 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
   float4* zc = ynext + 4;                        // [C] z of the current pivot row
   float2* invd = reinterpret_cast<float2*>(zc + 4);  // 1 / L_kk as df
   float4* thb = reinterpret_cast<float4*>(invd) + (NMAX + 1) / 2;  // [32][3] view-only values
+  float4* pq = thb + 96;  // lattice powers: [k - 1][32 R] P_r^k, then [kLatMax + k - 1][32 R] Q_r^k
+  // the views lie on an integer lattice (k_mom_check): A from the lattice powers
+  const bool lat = MOM && df_lat_f4(NMAX) > 0 && *((volatile int*)(p.counters + 10)) == 1;
 
   // coordinates (r, l) of this lane's slots, packed as r * 256 + l.  An unused slot
   // (entry number >= E) gets (N, N): it reads Arow[N] / col[N], which lie inside this
@@ -322,6 +334,22 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
       __syncwarp();
     }
 
+    if (lat) {
+      // P_r^k and Q_r^k from the exact-piece phases k d_r w_x, k d_r w_y; each lane reads
+      // only its own entries back, so no barrier is needed
+#pragma unroll
+      for (int h = 0; h < R; ++h) {
+        if (lane + 32 * h < N) {
+#pragma unroll 1
+          for (int k = 1; k <= kLatMax; ++k) {
+            const cx<Rdf> pk = cexp2pi(phase_r(theta_r((float)k, 0.f, fq, Rdf{}), dr[h]), tab);
+            const cx<Rdf> qk = cexp2pi(phase_r(theta_r(0.f, (float)k, fq, Rdf{}), dr[h]), tab);
+            pq[(k - 1) * 32 * R + 32 * h + lane] = pack(dfc{pk.re.v, pk.im.v});
+            pq[(kLatMax + k - 1) * 32 * R + 32 * h + lane] = pack(dfc{qk.re.v, qk.im.v});
+          }
+        }
+      }
+    }
     for (int j0 = 0; j0 < K; j0 += 32) {
       if constexpr (MOM) {
         // what depends on the view only (theta = u_j . w in exact pieces and as a double-float,
@@ -334,7 +362,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
           const float th2 = theta.hi * theta.hi, th3 = th2 * theta.hi;
           thb[3 * lane] = make_float4(t.p1, t.e1, t.p2, t.e2);
           thb[3 * lane + 1] = make_float4(t.g, theta.hi, theta.lo, th2);
-          thb[3 * lane + 2] = make_float4(th3, 0.f, 0.f, 0.f);
+          thb[3 * lane + 2] = make_float4(th3, ul.x, ul.y, 0.f);  // with the lattice coordinates
           acc_df(T1, theta);
           T2 += th2;
           T3 += th3;
@@ -347,12 +375,16 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
         ThetaX th;
         df theta = {0.f, 0.f};
         float th2 = 0.f, th3 = 0.f;
+        int ax = 0, by = 0;  // lattice coordinates of the view
         if constexpr (MOM) {
           const float4 q0 = thb[3 * jj], q1 = thb[3 * jj + 1];
           th = {q0.x, q0.y, q0.z, q0.w, q1.x};
           theta = {q1.y, q1.z};
           th2 = q1.w;
-          th3 = thb[3 * jj + 2].x;
+          const float4 q2 = thb[3 * jj + 2];
+          th3 = q2.x;
+          ax = (int)q2.y;
+          by = (int)q2.z;
         } else {
           const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
           th = theta_r(uj.x, uj.y, fq, Rdf{});
@@ -367,7 +399,23 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
           const int r = lane + 32 * h;
           aR[h] = {{0.f, 0.f}, {0.f, 0.f}};
           if (r < N) {
-            const cx<Rdf> a = cexp2pi(phase_r(th, dr[h]), tab);
+            cx<Rdf> a;
+            if (lat) {
+              // A_jr = P_r^a Q_r^b (conjugates for negative powers), one double-float product;
+              // terms of magnitude <= 1, summed with the sloppy double-word addition
+              dfc pa = {{1.f, 0.f}, {0.f, 0.f}}, qb = {{1.f, 0.f}, {0.f, 0.f}};
+              if (ax != 0) pa = unpack(pq[(abs(ax) - 1) * 32 * R + 32 * h + lane]);
+              if (by != 0) qb = unpack(pq[(kLatMax + abs(by) - 1) * 32 * R + 32 * h + lane]);
+              if (ax < 0) pa.im = df_neg(pa.im);
+              if (by < 0) qb.im = df_neg(qb.im);
+              const df p1 = df_mul(pa.re, qb.re), p2 = df_neg(df_mul(pa.im, qb.im));
+              const df q1 = df_mul(pa.re, qb.im), q2 = df_mul(pa.im, qb.re);
+              const df r1 = two_sum(p1.hi, p2.hi), r2 = two_sum(q1.hi, q2.hi);
+              a = {{fast_two_sum(r1.hi, __fadd_rn(r1.lo, __fadd_rn(p1.lo, p2.lo)))},
+                   {fast_two_sum(r2.hi, __fadd_rn(r2.lo, __fadd_rn(q1.lo, q2.lo)))}};
+            } else {
+              a = cexp2pi(phase_r(th, dr[h]), tab);
+            }
             aR[h] = {a.re.v, a.im.v};
             // A - 1: the subtraction of the high word is exact (TwoSum)
             const df t = two_sum(a.re.v.hi, -1.f);
