@@ -203,6 +203,37 @@ __global__ void k_mom_check(const float* __restrict__ d, int N, const float* __r
     lattice = lattice && ux == rintf(ux) && uy == rintf(uy) && fabsf(ux) <= (float)kLatMax && fabsf(uy) <= (float)kLatMax;
   }
   lattice = __all_sync(0xffffffffu, lattice);
+  // the views fill the rectangle [a0, a1] x [b0, b1] of the lattice, each point once
+  constexpr int kSide = 2 * kLatMax + 1;
+  __shared__ int cell[kSide * kSide];
+  for (int i = lane; i < kSide * kSide; i += 32) cell[i] = 0;
+  int a0 = kLatMax, a1 = -kLatMax, b0 = kLatMax, b1 = -kLatMax;
+  __syncwarp();
+  if (lattice) {
+    for (int j = lane; j < K; j += 32) {
+      const int ux = (int)u[2 * j], uy = (int)u[2 * j + 1];
+      atomicAdd(&cell[(uy + kLatMax) * kSide + ux + kLatMax], 1);
+      a0 = min(a0, ux);
+      a1 = max(a1, ux);
+      b0 = min(b0, uy);
+      b1 = max(b1, uy);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 = min(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+    a1 = max(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+    b0 = min(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+    b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+  }
+  __syncwarp();
+  bool grid = lattice && K > 0 && K == (a1 - a0 + 1) * (b1 - b0 + 1);
+  if (grid)
+    for (int i = lane; i < K; i += 32) {
+      const int na = a1 - a0 + 1;
+      grid = grid && cell[(b0 + i / na + kLatMax) * kSide + a0 + i % na + kLatMax] == 1;
+    }
+  grid = __all_sync(0xffffffffu, grid);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
@@ -215,6 +246,8 @@ __global__ void k_mom_check(const float* __restrict__ d, int N, const float* __r
     const float x = 6.2831853f * (emax - emin) * 1.0001f * umax * 0.70710678f + 1e-30f;
     counters[8] = (all_finite && N <= 64 && x <= kMomXLim) ? 1 : 0;
     counters[10] = (all_finite && lattice) ? 1 : 0;
+    counters[11] = (all_finite && grid) ? 1 : 0;
+    counters[12] = (a0 + kLatMax) | ((a1 + kLatMax) << 8) | ((b0 + kLatMax) << 16) | ((b1 + kLatMax) << 24);
   }
 }
 
@@ -256,6 +289,11 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
   float4* pq = thb + 96;  // lattice powers: [k - 1][32 R] P_r^k, then [kLatMax + k - 1][32 R] Q_r^k
   // the views lie on an integer lattice (k_mom_check): A from the lattice powers
   const bool lat = MOM && df_lat_f4(NMAX) > 0 && *((volatile int*)(p.counters + 10)) == 1;
+  // ... and fill a rectangle [ga0, ga1] x [gb0, gb1] of it: the moments of w factor over the axes
+  const bool grid = lat && *((volatile int*)(p.counters + 11)) == 1;
+  const int gbox = *((volatile int*)(p.counters + 12));
+  const int ga0 = (gbox & 255) - kLatMax, ga1 = ((gbox >> 8) & 255) - kLatMax;
+  const int gb0 = ((gbox >> 16) & 255) - kLatMax, gb1 = ((gbox >> 24) & 255) - kLatMax;
 
   // coordinates (r, l) of this lane's slots, packed as r * 256 + l.  An unused slot
   // (entry number >= E) gets (N, N): it reads Arow[N] / col[N], which lie inside this
@@ -434,6 +472,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
           }
         }
         if constexpr (MOM) {
+          if (grid) continue;  // the moments come from the axis sums after the view loop
           // w_jm = A_jm conj(A_j0) for this lane's m (A_j0 from lane 0) and the moments of w - 1
           const dfc a0 = unpack(shfl4(pack(aR[0]), 0));
 #pragma unroll
@@ -470,6 +509,91 @@ __global__ void __launch_bounds__(kDfWarps * 32, df_min_blocks(NMAX)) k_solve_df
         __syncwarp();
       }
       if constexpr (MOM) __syncwarp();  // the next chunk rewrites thb
+    }
+    if (MOM && grid) {
+      // Views filling the rectangle: w_jm = p_m^a q_m^b with p_m^a = P_m^a conj(P_0^a),
+      // q_m^b = Q_m^b conj(Q_0^b), and theta_j = a w_x + b w_y, so with p~ = p - 1, q~ = q - 1
+      //   sum_j a^s b^t (w_jm - 1) = X_st = SP_s sb_t + sa_s SQ_t + SP_s SQ_t,
+      //   SP_s = sum_a a^s p~^a, sa_s = sum_a a^s (SQ_t, sb_t over b),
+      // and M0 = X_00, M1 = w_x X_10 + w_y X_01, M2, M3 by the binomial expansion of theta^2,3
+      // (double-float to first order, FP32 beyond, as in the view loop).
+      __syncwarp();  // every lane reads row 0's powers
+      const df wxd = {fq.wx, fq.wx_lo}, wyd = {fq.wy, fq.wy_lo};
+#pragma unroll
+      for (int h = 0; h < R; ++h) {
+        if (lane + 32 * h >= N) continue;
+        dfc SP[2][2];     // [axis][s] for s = 0, 1 (double-float)
+        float2 SPf[2][4]; // [axis][s] high words, s = 0..3 (FP32)
+        float sg[2][4];   // sa_s, sb_s
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) {
+          SP[ax][0] = SP[ax][1] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            SPf[ax][t] = make_float2(0.f, 0.f);
+            sg[ax][t] = 0.f;
+          }
+          const int lo = ax == 0 ? ga0 : gb0, hi = ax == 0 ? ga1 : gb1;
+#pragma unroll 1
+          for (int a = lo; a <= hi; ++a) {
+            const float fa = (float)a;
+            sg[ax][0] += 1.f;
+            sg[ax][1] += fa;
+            sg[ax][2] += fa * fa;
+            sg[ax][3] += fa * fa * fa;
+            if (a == 0) continue;
+            const int row = (ax * kLatMax + abs(a) - 1) * 32 * R;
+            dfc pm = unpack(pq[row + 32 * h + lane]), p0 = unpack(pq[row]);
+            if (a < 0) {
+              pm.im = df_neg(pm.im);
+              p0.im = df_neg(p0.im);
+            }
+            const df wr = sadd_df(df_mul(pm.re, p0.re), df_mul(pm.im, p0.im));
+            const df wi = sadd_df(df_mul(pm.im, p0.re), df_neg(df_mul(pm.re, p0.im)));
+            const df t = two_sum(wr.hi, -1.f);
+            const df wm1r = two_sum(t.hi, __fadd_rn(t.lo, wr.lo));
+            acc_df(SP[ax][0].re, wm1r);
+            acc_df(SP[ax][0].im, wi);
+            acc_df(SP[ax][1].re, df_mul_f(wm1r, fa));
+            acc_df(SP[ax][1].im, df_mul_f(wi, fa));
+            float pw = 1.f;
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2) {
+              SPf[ax][s2].x = fmaf(pw, wm1r.hi, SPf[ax][s2].x);
+              SPf[ax][s2].y = fmaf(pw, wi.hi, SPf[ax][s2].y);
+              pw *= fa;
+            }
+          }
+        }
+        // double-float X_00, X_10, X_01
+        auto xd = [&](int s1, int t1) -> dfc {
+          const dfc& P = SP[0][s1];
+          const dfc& Q = SP[1][t1];
+          const df pr = df_mul(P.re, Q.re), pi = df_mul(P.im, Q.im);
+          const df qr = df_mul(P.re, Q.im), qi = df_mul(P.im, Q.re);
+          dfc x;
+          x.re = df_add(df_add(df_mul_f(P.re, sg[1][t1]), df_mul_f(Q.re, sg[0][s1])), df_sub(pr, pi));
+          x.im = df_add(df_add(df_mul_f(P.im, sg[1][t1]), df_mul_f(Q.im, sg[0][s1])), df_add(qr, qi));
+          return x;
+        };
+        auto xf = [&](int s1, int t1) -> float2 {
+          const float2 P = SPf[0][s1], Q = SPf[1][t1];
+          return make_float2(fmaf(P.x, sg[1][t1], fmaf(Q.x, sg[0][s1], fmaf(P.x, Q.x, -P.y * Q.y))),
+                             fmaf(P.y, sg[1][t1], fmaf(Q.y, sg[0][s1], fmaf(P.x, Q.y, P.y * Q.x))));
+        };
+        M0[h] = xd(0, 0);
+        const dfc x10 = xd(1, 0), x01 = xd(0, 1);
+        M1[h].re = df_add(df_mul(wxd, x10.re), df_mul(wyd, x01.re));
+        M1[h].im = df_add(df_mul(wxd, x10.im), df_mul(wyd, x01.im));
+        const float wx = fq.wx, wy = fq.wy;
+        const float2 x20 = xf(2, 0), x11 = xf(1, 1), x02 = xf(0, 2);
+        M2[h] = make_float2(wx * wx * x20.x + 2.f * wx * wy * x11.x + wy * wy * x02.x,
+                            wx * wx * x20.y + 2.f * wx * wy * x11.y + wy * wy * x02.y);
+        const float2 x30 = xf(3, 0), x21 = xf(2, 1), x12 = xf(1, 2), x03 = xf(0, 3);
+        const float c30 = wx * wx * wx, c21 = 3.f * wx * wx * wy, c12 = 3.f * wx * wy * wy, c03 = wy * wy * wy;
+        M3[h] = make_float2(c30 * x30.x + c21 * x21.x + c12 * x12.x + c03 * x03.x,
+                            c30 * x30.y + c21 * x21.y + c12 * x12.y + c03 * x03.y);
+      }
     }
     if constexpr (MOM) {
       // the sums of theta^p over the views, from the lanes' partial sums
