@@ -441,13 +441,13 @@ def serving_leg(device, n_requests=2000, rates=(2000.0, 20000.0), budget=2.5e9, 
                               0.0 if view else float(rng.uniform(0, 3)), t_arrival=t))
         return tr
 
-    def run(trace):
+    def run(trace, admissions=True):
         next_fid = [max(store.entries) + 1]
         picks = rng.integers(0, 1 << 30, len(trace))
         orig_submit = srv.submit
 
         def submit(r):
-            if r.rid > 0 and r.rid % 500 == 0:
+            if admissions and r.rid > 0 and r.rid % 500 == 0:
                 try:
                     admit(next_fid[0])
                 except Exception:  # every resident FDL in use: no room this time
@@ -485,6 +485,17 @@ def serving_leg(device, n_requests=2000, rates=(2000.0, 20000.0), budget=2.5e9, 
     if hbm_gbs:
         sat["hbm_frac"] = sat["alg_gbs"] / hbm_gbs
     out["saturation"] = sat
+    # the same burst without admissions, each batch's device time recorded: the render's own
+    # rate (device time during which a batch ran, the two batch streams overlapping)
+    srv.timeline = []
+    ren = run(make_trace(lambda i: 0.0), admissions=False)
+    ren["busy_ms"] = srv.busy_ms()
+    ren["alg_gbs_device"] = ren["alg_bytes"] / (ren["busy_ms"] / 1e3) / 1e9
+    ren["requests_per_fdl_per_batch"] = float(np.mean([t[3] for t in srv.timeline])) / len(store.entries)
+    srv.timeline = None
+    if hbm_gbs:
+        ren["hbm_frac_device"] = ren["alg_gbs_device"] / hbm_gbs
+    out["saturation_render_only"] = ren
     out["fdls_resident"] = len(store.entries)
     out["fdl_bytes"] = store.bytes_used
     out["evictions"] = evicted[0]
@@ -961,7 +972,7 @@ def main():
     # roofline: the high-precision solve (dominant kernel) on the method's flops; the DFT and
     # render stages against HBM
     rl = roofline_entry(legs, clk, moment_form_applies(u, d))
-    stage_rl = stage_rooflines(legs)
+    stage_rl = stage_rooflines(legs, clk)
     line = {
         "metric": METRIC, "value": value, "unit": "Mfreq/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -1000,13 +1011,17 @@ def main():
         hbm, src = measured_hbm()
         leg("serving", lambda: serving_leg(device, hbm_gbs=hbm))
     if rank == 0 and not args.no_serve and "error" not in line["serving"]:
-        sat = line["serving"]["saturation"]
-        line["roofline_stages"].append({"stage": "serving at saturation (2,000 mixed-size requests at once)",
-                                        "kernel": "k_render_cols (x2) + k_irfft_rows_req", "bound": "hbm",
-                                        "achieved": sat["alg_gbs"], "peak": hbm, "unit": "GB/s",
-                                        "frac": sat["alg_gbs"] / hbm, "algorithmic_bytes": sat["alg_bytes"],
-                                        "traffic": None, "peak_source": src,
-                                        "note": "host wall time of the whole trace, batches of up to 32"})
+        sat = line["serving"]["saturation_render_only"]
+        line["roofline_stages"].append({"stage": "serving render at saturation (2,000 mixed-size requests at once, "
+                                                 "batches of up to 32)",
+                                        "kernel": "k_render_gate + k_render_cols (x2) + k_irfft_rows_req "
+                                                  "(+ the tiled passes, gated off)", "bound": "hbm",
+                                        "achieved": sat["alg_gbs_device"], "peak": hbm, "unit": "GB/s",
+                                        "frac": sat["alg_gbs_device"] / hbm, "algorithmic_bytes": sat["alg_bytes"],
+                                        "traffic": None, "peak_source": src, "ms": sat["busy_ms"],
+                                        "note": "device time of the batches (union of their intervals); "
+                                                "algorithmic bytes: each FDL of a batch read once, each image "
+                                                "written once"})
         line["latency"]["serving_p50_ms"] = line["serving"]["poisson_2000"]["p50_ms"]
         line["latency"]["serving_p99_ms"] = line["serving"]["poisson_2000"]["p99_ms"]
         torch.cuda.empty_cache()
@@ -1024,33 +1039,6 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def df_ops_per_frequency(K, N, C, moment=True):
-    """FP32 operations of the double-float solve at one frequency, counted from its formulas
-    (each term: operations per item x items):
-
-    - phase d (u.w) from exact pieces 49 and double-float exp 168, per (view, layer);
-    - A - 1: 13 per (view, layer); right-hand side 56 per (view, layer, channel);
-    - Gram, moment form (disparities on a grid up to rounding): w_jm = A_jm conj(A_j0) and
-      the four moments of w - 1 133 per (view, layer), 49 per view, assembly 145 per
-      off-diagonal entry; direct form: 54 per (off-diagonal entry, view) plus the A - 1
-      sums 30 per (view, layer);
-    - sum of b: 20 per (view, channel); Cholesky 56 per (r, l, k) update, 70 per pivot,
-      14 per scaled entry; condition estimate 3 x 2 x 8 per entry; triangular solves 56 per
-      (entry, channel) in each direction plus 14 per (row, channel)."""
-    nk = N * K
-    offd = N * (N - 1) // 2
-    work = nk * (49 + 168) + nk * 13 + nk * C * 56
-    if moment:
-        work += nk * 133 + K * 49 + offd * 145
-    else:
-        work += offd * K * 54 + nk * 30
-    work += K * C * 20 + N * C * 40
-    work += ((N ** 3 - N) // 6) * 56 + N * 70 + offd * 14
-    work += 3 * 2 * offd * 8
-    work += 2 * offd * C * 56 + 2 * N * C * 14
-    return work
-
-
 def moment_form_applies(u, d):
     """The device-side test of the solve: 2 pi (spread of d about its grid) max|u| / sqrt(2) <= 1e-4."""
     d = np.asarray(d, np.float64)
@@ -1065,11 +1053,15 @@ def moment_form_applies(u, d):
 # Gram 14.6k, A 14.6k, right-hand side 58.3k, Cholesky 36k, solves 21.6k.
 FP32_METHOD_FLOPS_PER_FREQUENCY = 145_000
 
-# DRAM bytes (read + write) per frequency of k_solve_df<30, 15, moment form> from an ncu capture
-# of the all-frequency launch (bench.py --case df512: 271.07 MB read, 79.06 MB written).  The
-# algorithmic bytes are the K x C spectrum values read and the N x C layer values written,
-# 8 bytes each: 2,664.
-DF_DRAM_BYTES_PER_FREQUENCY = (271.074304e6 + 79.06048e6) / 131_584
+# From an ncu capture of the all-frequency k_solve_df<30, 15, moment form> launch (bench.py
+# --case df512): DRAM bytes (read + write) and warp instructions per frequency.  The algorithmic
+# bytes are the K x C spectrum values read and the N x C layer values written, 8 bytes each:
+# 2,664 per frequency.
+DF_DRAM_BYTES_PER_FREQUENCY = (270.752e6 + 79.548672e6) / 131_584
+DF_WARP_INSTRUCTIONS_PER_FREQUENCY = 9_554_976_035 / 131_584
+# The FP32 solve (k_solve_f32<32>, the pass with estimates, bench.py --case step): DRAM bytes per
+# launch over all 131,584 frequencies.
+F32_DRAM_BYTES = 257.351168e6 + 73.79072e6
 
 
 # ------------------------------------------------------------------ bounded cases for profilers
@@ -1162,13 +1154,14 @@ def roofline_entry(legs, clk, moment):
     achieved = the method's own flops (an FP32 solve with a Toeplitz Gram: 145 kflop per
     frequency on this workload) per second of the all-frequency double-float launch; peak =
     152 SMs x 128 FP32 lanes x 2 flop per FMA x the median SM clock sampled in the run.
-    issue_frac: the FP32 operations the double-float arithmetic issues for that work (its
-    precision costs ~12 operations per method flop) against one operation per lane and cycle."""
+    issue_frac: the warp instructions the kernel issues (ncu count per frequency) per second of
+    the same launch against the 4 issue slots of each SM per cycle: the double-float
+    arithmetic's own bound."""
     ms = legs["solve_df_all_ms"]
     mhz = clk.get("sm_mhz") or 2070.0
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     achieved = FP32_METHOD_FLOPS_PER_FREQUENCY * q_half() / (ms / 1e3) / 1e12
-    ops = df_ops_per_frequency((2 * GRID + 1) ** 2, N, C, moment)
+    wi = DF_WARP_INSTRUCTIONS_PER_FREQUENCY if moment else None
     form = "moment-form Gram" if moment else "direct Gram"
     return {"kernel": f"k_solve_df (double-float per-frequency solve, {form}, all 131,584 frequencies)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -1177,8 +1170,8 @@ def roofline_entry(legs, clk, moment):
             "algorithmic_bytes": ((2 * GRID + 1) ** 2 + N) * C * 8 * q_half(),
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop (FMA) x {mhz:.0f} MHz (median SM clock in the run)",
             "method_flops_per_frequency": FP32_METHOD_FLOPS_PER_FREQUENCY,
-            "issue_ops_per_frequency": ops,
-            "issue_frac": ops * q_half() / (ms / 1e3) / (152 * 128 * mhz * 1e6)}
+            "warp_instructions_per_frequency": wi,
+            "issue_frac": wi * q_half() / (ms / 1e3) / (152 * 4 * mhz * 1e6) if wi else None}
 
 
 def roofline_hbm(stage, kernel, alg_bytes, ms, traffic=None):
@@ -1188,24 +1181,35 @@ def roofline_hbm(stage, kernel, alg_bytes, ms, traffic=None):
             "frac": ach / hbm, "algorithmic_bytes": alg_bytes, "traffic": traffic, "ms": ms, "peak_source": src}
 
 
-def stage_rooflines(legs):
-    """HBM roofline of the forward DFT and of the fused render + inverse DFT (algorithmic bytes:
-    every input read once, every output written once)."""
+def stage_rooflines(legs, clk):
+    """The FP32 solve against the FP32 pipe (method flops as in roofline_entry), and the HBM
+    roofline of the forward DFT and of the renders (algorithmic bytes: every input read once,
+    every output written once).  The 81 views and the 32 refocused images each read one FDL,
+    so the device gate sends them to the tiled path (render, inverse column pass, row pass)."""
     K = (2 * GRID + 1) ** 2
     img = C * H * W * 4
     layers = N * C * q_half() * 8
-    return [roofline_hbm("forward DFT of the 243 view images", "k_rfft_rows_df + k_fft_cols_df",
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    f32 = FP32_METHOD_FLOPS_PER_FREQUENCY * q_half() / (legs["solve_f32_all_ms"] / 1e3) / 1e12
+    tiled = "k_render + k_fft_cols<inverse> + k_irfft_rows"
+    return [{"stage": "FP32 solve of every frequency (no estimate)", "kernel": "k_solve_f32<32>", "bound": "alu",
+             "achieved": f32, "peak": peak, "unit": "TFLOP/s", "frac": f32 / peak,
+             "ms": legs["solve_f32_all_ms"], "traffic": F32_DRAM_BYTES,
+             "algorithmic_bytes": (K + N) * C * 8 * q_half(),
+             "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop (FMA) x {mhz:.0f} MHz"},
+            roofline_hbm("forward DFT of the 243 view images", "k_rfft_rows_df + k_fft_cols_df",
                          K * img + K * C * q_half() * 8, legs["rfft2_ms"], DFT_DRAM_BYTES),
-            roofline_hbm("render of the 81 input views", "k_render_cols (x2) + k_irfft_rows_req",
-                         layers + K * img, legs["render81_ms"], RENDER81_DRAM_BYTES),
-            roofline_hbm("32 refocused images (disc)", "k_render_cols (x2) + k_irfft_rows_req",
-                         layers + N_REFOCUS * img, legs["refocus32_ms"], None)]
+            roofline_hbm("render of the 81 input views", tiled, layers + K * img, legs["render81_ms"],
+                         RENDER81_DRAM_BYTES),
+            roofline_hbm("32 refocused images (disc)", tiled, layers + N_REFOCUS * img, legs["refocus32_ms"], None)]
 
 
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels (None: not
-# captured): the forward DFT's two passes from bench.py --case render81.
+# captured), all from bench.py --case render81: the forward DFT's two passes, and the tiled
+# render of the 81 views (k_render, the inverse column pass, the row pass).
 DFT_DRAM_BYTES = (254.834944e6 + 209.893632e6) + (254.8416e6 + 201.214976e6)
-RENDER81_DRAM_BYTES = None
+RENDER81_DRAM_BYTES = (99.3e6 + 201.2e6) + (255.831552e6 + 193.479168e6) + (254.873088e6 + 212.408064e6)
 
 
 if __name__ == "__main__":

@@ -172,7 +172,7 @@ class _Batch:
             self._body()
         self.stream.synchronize()
 
-    def launch(self, reqs: list[Request], store: FdlStore, pts: dict, batch_id: int = -1):
+    def launch(self, reqs: list[Request], store: FdlStore, pts: dict, batch_id: int = -1, timeline=None):
         # requests of one FDL side by side: the fused render's consecutive CTAs then read the
         # same strip of layer values, which stays in L2 between them
         reqs = sorted(reqs, key=lambda r: r.fid)
@@ -197,8 +197,15 @@ class _Batch:
         for ev in waits.values():
             self.stream.wait_event(ev)
         with torch.cuda.stream(self.stream):
+            if timeline is not None:
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(self.stream)
             self.graph.replay()
             self.done.record(self.stream)
+            if timeline is not None:
+                t1.record(self.stream)
+                timeline.append((t0, t1, self.alg_bytes, len(reqs)))
         self.requests = list(reqs)
         self.busy = True
 
@@ -229,6 +236,9 @@ class Server:
         self.pts = {}
         self.alg_bytes = 0  # algorithmic bytes of every launched batch (layers once per FDL, images)
         self.launches = 0
+        # with a list here, every launch appends (start event, end event, algorithmic bytes,
+        # requests) recorded on its stream: device time of the batches (busy_ms)
+        self.timeline: list | None = None
 
     def submit(self, r: Request):
         # a queued request holds its FDL: admissions do not evict it before it has rendered
@@ -278,11 +288,29 @@ class Server:
                 reqs.append(self.queue.popleft())
             if not reqs:
                 break
-            b.launch(reqs, self.store, self.pts, self.launches)
+            b.launch(reqs, self.store, self.pts, self.launches, self.timeline)
             self.alg_bytes += b.alg_bytes
             self.launches += 1
             launched += 1
         return launched
+
+    def busy_ms(self) -> float:
+        """Device time during which at least one recorded batch ran (the union of the
+        batches' [start, end] intervals; the batch streams overlap).  Synchronises."""
+        if not self.timeline:
+            return 0.0
+        for _, t1, _, _ in self.timeline:
+            t1.synchronize()
+        ref = self.timeline[0][0]
+        iv = sorted((ref.elapsed_time(t0), ref.elapsed_time(t1)) for t0, t1, _, _ in self.timeline)
+        total, cur0, cur1 = 0.0, iv[0][0], iv[0][1]
+        for a, b in iv[1:]:
+            if a > cur1:
+                total += cur1 - cur0
+                cur0, cur1 = a, b
+            else:
+                cur1 = max(cur1, b)
+        return total + cur1 - cur0
 
     def drain(self, timeout_s: float = 30.0):
         """Run ticks until every queued request has completed (bounded wait)."""
