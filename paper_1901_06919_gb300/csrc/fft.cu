@@ -1,6 +1,6 @@
-// 2D real DFTs of the FDL path (Sec. V-A: the DFT of every input view;
-// Sec. VI-A: the inverse DFT of a rendered spectrum; Sec. VII: only the
-// non-negative-kx half is kept).
+// Inverse 2D real DFT of the FDL path in FP32 (Sec. VI-A: the inverse DFT of a
+// rendered spectrum; Sec. VII: only the non-negative-kx half is kept); the
+// forward DFT of the views is in fft_df.cu.
 //
 // Layout of a row-transformed image (the "split" layout): W/2 complex per row
 // (pitch W/2, so every row starts on a 16-byte boundary), element 0 packing
@@ -21,57 +21,8 @@ namespace fdl {
 
 namespace {
 
-// ---------------------------------------------------------------- row R2C
-// CTA of T = max(256, M/4) threads transforms R = T / (M/4) consecutive rows.
-template <int MAXB>
-__global__ void __launch_bounds__(512) k_rfft_rows(const float* __restrict__ in, float2* __restrict__ out,
-                                                   long long nrows, int W, int logM) {
-  extern __shared__ float2 sm[];
-  const int M = W >> 1;
-  float2* tw = sm;
-  float2* data = sm + M;
-  const int q = M >> 2;
-  const int R = blockDim.x / q;
-  const long long row0 = (long long)blockIdx.x * R;
-  make_twiddles(tw, M);
-  const long long rows_here = min((long long)R, nrows - row0);
-  const int nf4 = R * (W >> 2);
-  const int valid = (int)rows_here * (W >> 2);
-  const float4* src = reinterpret_cast<const float4*>(in + row0 * W);
-  for (int e = threadIdx.x; e < nf4; e += blockDim.x) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e < valid) v = __ldg(src + e);
-    reinterpret_cast<float4*>(data)[e] = v;  // z[n] = x[2n] + i x[2n+1]
-  }
-  __syncthreads();
-  int lognfft = 0;
-  while ((1 << lognfft) < R) ++lognfft;
-  stockham<false, MAXB>(data, tw, M, logM, R, lognfft, M, 1);
-  // Z = E + i O with E, O the DFTs of the even and odd samples;
-  // X[k] = E[k] + exp(-2 pi i k / W) O[k], X[M] = E[0] - O[0].
-  for (int e = threadIdx.x; e < R * M; e += blockDim.x) {
-    const int r = e >> logM, k = e & (M - 1);
-    const long long row = row0 + r;
-    if (row >= nrows) continue;
-    const float2* z = data + r * M;
-    const float2 Zk = z[k];
-    float2 o;
-    if (k == 0) {
-      o = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
-    } else {
-      const float2 Zm = z[M - k];
-      const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
-      const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
-      float sn, cs;
-      sincospif(-(float)k / (float)M, &sn, &cs);
-      o = cadd(E, cmul(make_float2(cs, sn), O));
-    }
-    out[row * M + k] = o;
-  }
-}
-
 // ---------------------------------------------------------------- row C2R
-constexpr int kMaxRowsPerCta = 128;  // R = max(256, M/4) / (M/4) with M >= 8
+constexpr int kMaxRowsPerCta = 128;  // R = MAXB T / (M/4), T = max(256, M/4)
 template <int MAXB>
 __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ in, float* __restrict__ out,
                                                     long long nrows, int H, int W, int logM, float scale,
@@ -85,11 +36,13 @@ __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ i
   float2* tw = sm;
   float2* data = sm + M;
   const int q = M >> 2;
-  const int R = blockDim.x / q;
+  const int R = MAXB * blockDim.x / q;
   const long long row0 = (long long)blockIdx.x * R;
   if (count) nrows = min(nrows, (long long)(*count) * C * H);
   if (row0 >= nrows) return;
   make_twiddles(tw, M);
+  float2 h;  // exp(i pi / M)
+  sincospif(1.f / (float)M, &h.y, &h.x);
   // rows of requests the render skipped are not written
   for (int rr = threadIdx.x; rr < R; rr += blockDim.x)
     rowok[rr] = req == nullptr || row0 + rr >= nrows || request_ok(req[(row0 + rr) / H / C], C, H, W, nmax, true);
@@ -102,9 +55,10 @@ __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ i
   __syncthreads();
   // Z[k] = E[k] + i O[k], E[k] = X[k] + conj X[M-k],
   // O[k] = (X[k] - conj X[M-k]) exp(+2 pi i k / W); X[0], X[M] are packed in element 0.
-  float2 zk[8];
-  int cnt = 0;
-  for (int e = threadIdx.x; e < R * M; e += blockDim.x, ++cnt) {
+  float2 zk[4 * MAXB];  // R * M = 4 * MAXB * blockDim.x elements, 4 * MAXB per thread
+#pragma unroll
+  for (int i = 0; i < 4 * MAXB; ++i) {
+    const int e = threadIdx.x + i * blockDim.x;
     const int r = e >> logM, k = e & (M - 1);
     const float2* X = data + r * M;
     float2 Z;
@@ -115,17 +69,14 @@ __global__ void __launch_bounds__(512) k_irfft_rows(const float2* __restrict__ i
       const float2 a = X[k], bm = X[M - k];
       const float2 E = make_float2(a.x + bm.x, a.y - bm.y);
       float2 O = make_float2(a.x - bm.x, a.y + bm.y);
-      float sn, cs;
-      sincospif((float)k / (float)M, &sn, &cs);
-      O = cmul(O, make_float2(cs, sn));
+      O = cmul(O, half_twiddle_conj(tw, k, h));
       Z = make_float2(E.x - O.y, E.y + O.x);
     }
-    if (cnt < 8) zk[cnt] = Z;
+    zk[i] = Z;
   }
   __syncthreads();
-  cnt = 0;
-  for (int e = threadIdx.x; e < R * M; e += blockDim.x, ++cnt)
-    if (cnt < 8) data[e] = zk[cnt];
+#pragma unroll
+  for (int i = 0; i < 4 * MAXB; ++i) data[threadIdx.x + i * blockDim.x] = zk[i];
   __syncthreads();
   int lognfft = 0;
   while ((1 << lognfft) < R) ++lognfft;
@@ -195,25 +146,6 @@ __global__ void __launch_bounds__(512) k_fft_cols(SpecView in, SpecView out, int
     __syncthreads();
   }
   stockham<INV, MAXB>(data, tw, H, logH, SW, logSW, 1, SW);
-  if (!INV && c0 == 0) {
-    // unpack column 0: Z = F0 + i FN with F0, FN DFTs of real columns
-    float2 f0v[8];
-    int cnt = 0;
-    float2* nyq = out.nyq + img * out.nyq_img_stride;
-    for (int ky = threadIdx.x; ky < H; ky += blockDim.x, ++cnt) {
-      const int km = (H - ky) & (H - 1);
-      const float2 z = data[ky * SW], zm = data[km * SW];
-      const float2 f0 = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-      const float2 fn = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-      nyq[(long long)ky * out.nyq_stride] = fn;
-      if (cnt < 8) f0v[cnt] = f0;
-    }
-    __syncthreads();
-    cnt = 0;
-    for (int ky = threadIdx.x; ky < H; ky += blockDim.x, ++cnt)
-      if (cnt < 8) data[ky * SW] = f0v[cnt];
-    __syncthreads();
-  }
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int y = e >> logSW, c = e & (SW - 1);
     out.main[img * out.img_stride + (long long)y * out.pitch + c0 + c] = data[e];
@@ -274,35 +206,29 @@ int ilog2(int v) {
   return l;
 }
 
-cudaError_t launch_rfft_rows(const float* in, float2* out, long long nrows, int W, cudaStream_t st) {
-  const int M = W / 2;
-  const int T = (M / 4 > 256) ? M / 4 : 256;
-  const int R = T / (M / 4);
-  const size_t smem = (size_t)(M + R * M) * sizeof(float2);
-  const long long grid = (nrows + R - 1) / R;
-  cudaError_t e = set_smem((const void*)k_rfft_rows<1>, smem);
-  if (e != cudaSuccess) return e;
-  k_rfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, W, ilog2(M));
-  return cudaGetLastError();
-}
-
 cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int H, int W, float scale,
                               const fdl_request* req, const int* count, int C, cudaStream_t st, int nmax,
                               const int* gate) {
+  // two radix-4 butterflies per thread and pass (R = 2T / (M/4) rows per CTA), one for M < 16
+  // where that would exceed kMaxRowsPerCta rows
   const int M = W / 2;
   const int T = (M / 4 > 256) ? M / 4 : 256;
-  const int R = T / (M / 4);
+  const int mb = M >= 16 ? 2 : 1;
+  const int R = mb * T / (M / 4);
   const size_t smem = (size_t)(M + R * M) * sizeof(float2);
   const long long grid = (nrows + R - 1) / R;
-  cudaError_t e = set_smem((const void*)k_irfft_rows<1>, smem);
-  if (e != cudaSuccess) return e;
-  k_irfft_rows<1><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, H, W, ilog2(M), scale, req, count, C, nmax,
-                                                    gate);
+  cudaError_t e = cudaSuccess;
+#define FDL_ROWS(MB)                                                                                  \
+  {                                                                                                   \
+    e = set_smem((const void*)k_irfft_rows<MB>, smem);                                                \
+    if (e != cudaSuccess) return e;                                                                   \
+    k_irfft_rows<MB><<<(unsigned)grid, T, smem, st>>>(in, out, nrows, H, W, ilog2(M), scale, req, count, C, \
+                                                      nmax, gate);                                    \
+  }
+  if (mb == 2) FDL_ROWS(2)
+  else FDL_ROWS(1)
+#undef FDL_ROWS
   return cudaGetLastError();
-}
-
-cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int W, cudaStream_t st) {
-  return launch_cols<false>(in, out, nimg, H, W, nullptr, 1, st);
 }
 
 cudaError_t launch_fft_cols_inv(SpecView in, float2* out, int nimg, int H, int W, const int* count, int C,

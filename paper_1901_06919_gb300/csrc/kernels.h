@@ -13,13 +13,6 @@ namespace fdl {
 cudaError_t set_smem(const void* kernel, size_t bytes);
 
 // ---- FFT (fft.cu) ----------------------------------------------------------
-// Row pass of the 2D real DFT: nrows rows of W floats -> W/2 complex each
-// (element 0 packs X[0] + i X[W/2]), rows written with stride W/2.
-cudaError_t launch_rfft_rows(const float* in, float2* out, long long nrows, int W, cudaStream_t st);
-// Column pass: forward DFT along H of a row-transformed stack held in the
-// split layout `in` (kx = 0 column packed), written unpacked to `out`
-// (may alias `in`).
-cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int W, cudaStream_t st);
 // Inverse column pass: half spectra `in` (any layout) -> split layout `out`
 // with pitch W/2 and the kx = 0 / kx = W/2 columns packed after taking
 // their Hermitian parts.
@@ -27,9 +20,13 @@ cudaError_t launch_fft_cols_fwd(SpecView in, SpecView out, int nimg, int H, int 
 // gate (nullable, device): the inverse passes return at once unless *gate != 0.
 cudaError_t launch_fft_cols_inv(SpecView in, float2* out, int nimg, int H, int W, const int* count, int C,
                                 cudaStream_t st, const int* gate = nullptr);
-// The same forward passes with double-float arithmetic inside each pass
-// (fft_df.cu); `tables` = double-float twiddles of lengths W then H, built by
-// launch_twiddle_tables into fft_df_table_bytes(H, W) of workspace.
+// Forward passes, with double-float arithmetic inside each pass (fft_df.cu).
+// Row pass: nrows rows of W floats -> W/2 complex each (element 0 packs
+// X[0] + i X[W/2]), rows written with stride W/2.  Column pass: forward DFT
+// along H of a row-transformed stack held in the split layout `in` (kx = 0
+// column packed), written unpacked to `out` (may alias `in`).  `tables` =
+// double-float twiddles of lengths W then H, built by launch_twiddle_tables
+// into fft_df_table_bytes(H, W) of workspace.
 size_t fft_df_table_bytes(int H, int W);
 cudaError_t launch_twiddle_tables(float4* tables, int H, int W, cudaStream_t st);
 cudaError_t launch_rfft_rows_df(const float* in, float2* out, long long nrows, int W, const float4* tables,

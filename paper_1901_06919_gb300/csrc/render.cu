@@ -109,7 +109,7 @@ constexpr int kTileMaxLC = 256;  // N * C of an FDL staged in shared memory
 // SHIFTS: the request's per-layer shifts P_k in shb (the relaxed model), else u0 d_k.
 // AP: 0 no aperture factor (pinhole, or a disc of radius 0), 1 disc, 2 drawn (table),
 // 3 square or points.
-template <bool TILE, bool SHIFTS, int AP>
+template <int CC, bool TILE, bool SHIFTS, int AP>
 __device__ __forceinline__ void render_terms_t(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                                float wx, float wabs, long long plane, long long off, bool valid,
                                                const float2* tile, const float* dsh, int lane, float2 acc[4],
@@ -141,13 +141,14 @@ __device__ __forceinline__ void render_terms_t(const fdl_request& r, int k0, int
     }
     if (valid) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (c < C) cfma(acc[c], coef, TILE ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off));
+      for (int c = 0; c < CC; ++c)
+        if (CC < 4 || c < C)
+          cfma(acc[c], coef, TILE ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off));
     }
   }
 }
 
-template <bool TILE, bool SHIFTS>
+template <int CC, bool TILE, bool SHIFTS>
 __device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                                 float wx, float wabs, long long plane, long long off, bool valid,
                                                 const float2* tile, const float* dsh, int lane, float2 acc[4],
@@ -157,7 +158,7 @@ __device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, in
                  : r.aperture == FDL_AP_TABLE                                                 ? 2
                                                                                               : 3;
 #define FDL_TERMS(A) \
-  render_terms_t<TILE, SHIFTS, A>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq)
+  render_terms_t<CC, TILE, SHIFTS, A>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq)
   if (ap == 0) FDL_TERMS(0);
   else if (ap == 1) FDL_TERMS(1);
   else if (ap == 2) FDL_TERMS(2);
@@ -170,11 +171,12 @@ __device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, in
 // directly at every layer here: a recurrence across layers measured slower in this kernel
 // (a dependent chain per warp and request, and its set-up for the few layers each warp
 // takes when the layers of one request are split across warps).
+template <int CC>
 __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                              float wx, float wabs, long long plane, long long off, bool valid,
                                              const float2* tile, const float* dsh, int lane, float2 acc[4],
                                              const float2* __restrict__ shb, const Freq& fq) {
-#define FDL_AP(T, S) render_terms_ap<T, S>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, \
+#define FDL_AP(T, S) render_terms_ap<CC, T, S>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, \
                                           shb, fq)
   if (tile != nullptr) {
     if (shb != nullptr) FDL_AP(true, true);
@@ -186,6 +188,43 @@ __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int k
 #undef FDL_AP
 }
 
+// Two requests on the layer values staged in shared memory, pinhole (AP 0) or disc (AP 1), no
+// shift model: one pass over the layers loads each layer value once for both and keeps two
+// independent chains of phase, aperture and sums in flight.
+template <int CC, int AP>
+__device__ __forceinline__ void render_pair(const fdl_request& r1, const fdl_request& r2, int C, df th1, df th2,
+                                            float wabs, bool valid, const float2* tile, const float* dsh, int lane,
+                                            float2 acc1[4], float2 acc2[4]) {
+  const float z1 = 6.283185307f * r1.radius * wabs, z2 = 6.283185307f * r2.radius * wabs;
+  for (int k = 0; k < r1.N; ++k) {
+    const float dk = dsh[k];
+    float2 c1, c2;
+    __sincosf(6.28318531f * phase_from_theta(th1, dk), &c1.y, &c1.x);
+    __sincosf(6.28318531f * phase_from_theta(th2, dk), &c2.y, &c2.x);
+    if constexpr (AP == 1) {
+      c1 = cscale(c1, disc_hat(z1 * fabsf(r1.s - dk)));
+      c2 = cscale(c2, disc_hat(z2 * fabsf(r2.s - dk)));
+    }
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+        if (CC < 4 || c < C) {
+          const float2 v = tile[(k * C + c) * 32 + lane];
+          cfma(acc1[c], c1, v);
+          cfma(acc2[c], c2, v);
+        }
+      }
+    }
+  }
+}
+
+// the aperture class of a request for render_pair: 0 pinhole (or a disc of radius 0), 1 disc,
+// -1 anything else
+__device__ __forceinline__ int pair_class(const fdl_request& r) {
+  if (r.aperture == FDL_AP_PINHOLE || (r.aperture == FDL_AP_DISC && r.radius == 0.f)) return 0;
+  return r.aperture == FDL_AP_DISC ? 1 : -1;
+}
+
 // CTA: 32 consecutive stored bins (lane = bin) x 8 warps.
 //  * B >= 8 requests: warp w renders requests w, w + 8, ...; when every request reads
 //    the same FDL (and N*C <= tile_lc) the CTA first stages that FDL's layer values for
@@ -193,6 +232,7 @@ __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int k
 //  * B < 8 (single renders, small batches): the 8 / B warps given to a request split its
 //    layers and their partial sums are added through shared memory, so that one request
 //    still occupies the whole CTA.
+template <int CC>
 __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request* __restrict__ req, int B,
                                                               const int* __restrict__ count, int C, int H, int W,
                                                               int tile_lc, int nmax, SpecView out,
@@ -231,7 +271,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
       const fdl_request r = req[b];
       const df theta = df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, wxlo, r.u0y * wylo));
       const float2* shb = shifts ? reinterpret_cast<const float2*>(shifts) + (long long)b * r.N : nullptr;
-      render_terms(r, sl, G, C, theta, wy, wx, wabs, plane, off, valid, nullptr, nullptr, lane, acc, shb, fq);
+      render_terms<CC>(r, sl, G, C, theta, wy, wx, wabs, plane, off, valid, nullptr, nullptr, lane, acc, shb, fq);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) part[warp][c][lane] = acc[c];
@@ -253,7 +293,8 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   const float* L0 = req[0].layers;
   const int N0 = req[0].N;
   for (int b = threadIdx.x; b < Bact; b += blockDim.x)
-    if (req[b].layers != L0 || req[b].d != req[0].d || !request_ok(req[b], C, H, W, nmax, true)) uniform = 0;
+    if (req[b].layers != L0 || req[b].d != req[0].d || req[b].N != N0 || !request_ok(req[b], C, H, W, nmax, true))
+      uniform = 0;
   __syncthreads();
   const bool shared = uniform && N0 * C <= tile_lc && N0 <= 64;
   if (shared) {
@@ -279,12 +320,39 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
     }
     const fdl_request r = req[b];
     const df theta = df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, wxlo, r.u0y * wylo));
+    // this warp's next request along with this one when both read the staged layers with an
+    // aperture render_pair takes (the uniform test above checked it too)
+    const int b2 = b + kRenderWarps;
+    if (shared && shifts == nullptr && b2 < Bact) {
+      const fdl_request r2 = req[b2];
+      const int k1 = pair_class(r), k2 = pair_class(r2);
+      if (k1 >= 0 && k1 == k2) {
+        const df th2 =
+            df_add_f(df_add(two_prod(r2.u0x, wx), two_prod(r2.u0y, wy)), fmaf(r2.u0x, wxlo, r2.u0y * wylo));
+        float2 a1[4], a2[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a1[c] = a2[c] = make_float2(0.f, 0.f);
+        if (k1 == 0) render_pair<CC, 0>(r, r2, C, theta, th2, wabs, valid, tile, dsh, lane, a1, a2);
+        else render_pair<CC, 1>(r, r2, C, theta, th2, wabs, valid, tile, dsh, lane, a1, a2);
+        if (valid) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (c < C) {
+              *out.at((long long)b * C + c, ky, kx, M) = a1[c];
+              *out.at((long long)b2 * C + c, ky, kx, M) = a2[c];
+            }
+          }
+        }
+        b = b2;  // the loop's increment moves on past b2
+        continue;
+      }
+    }
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
     const float2* shb = shifts ? reinterpret_cast<const float2*>(shifts) + (long long)b * r.N : nullptr;
-    render_terms(r, 0, 1, C, theta, wy, wx, wabs, plane, off, valid, shared ? tile : nullptr, dsh, lane, acc, shb,
-                 fq);
+    render_terms<CC>(r, 0, 1, C, theta, wy, wx, wabs, plane, off, valid, shared ? tile : nullptr, dsh, lane, acc, shb,
+                     fq);
     if (valid) {
 #pragma unroll
       for (int c = 0; c < 4; ++c)
@@ -598,6 +666,8 @@ __global__ void __launch_bounds__(kRcThreads) k_irfft_rows_req(const fdl_request
   float2* tw = sm;
   float2* data = sm + (Wmax >> 1);
   make_twiddles(tw, M);
+  float2 h;  // exp(i pi / M)
+  sincospif(1.f / (float)M, &h.y, &h.x);
   const float2* in = slots + (long long)b * slot_elems;
   for (int e = threadIdx.x; e < R * M; e += blockDim.x) {
     const int rr = e >> logM;
@@ -621,9 +691,7 @@ __global__ void __launch_bounds__(kRcThreads) k_irfft_rows_req(const fdl_request
       const float2 a = X[k], bm = X[M - k];
       const float2 E = make_float2(a.x + bm.x, a.y - bm.y);
       float2 O = make_float2(a.x - bm.x, a.y + bm.y);
-      float sn, cs;
-      sincospif((float)k / (float)M, &sn, &cs);
-      O = cmul(O, make_float2(cs, sn));
+      O = cmul(O, half_twiddle_conj(tw, k, h));
       Z = make_float2(E.x - O.y, E.y + O.x);
     }
     zk[i] = Z;
@@ -674,10 +742,19 @@ cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* coun
   const int Qs = H * (W / 2 + 1);
   const int tile_lc = min(Nmax * C, kTileMaxLC);
   const size_t smem = (size_t)tile_lc * 32 * sizeof(float2);
-  cudaError_t e = set_smem((const void*)k_render, (size_t)kTileMaxLC * 32 * sizeof(float2));
-  if (e != cudaSuccess) return e;
-  k_render<<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, Nmax, out, shifts,
-                                                            status, gate);
+  cudaError_t e = cudaSuccess;
+  // the channel loop unrolled for one and three channels, predicated up to four otherwise
+#define FDL_RENDER(CC)                                                                                         \
+  {                                                                                                            \
+    e = set_smem((const void*)k_render<CC>, (size_t)kTileMaxLC * 32 * sizeof(float2));                        \
+    if (e != cudaSuccess) return e;                                                                            \
+    k_render<CC><<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, Nmax, out,  \
+                                                                  shifts, status, gate);                       \
+  }
+  if (C == 1) FDL_RENDER(1)
+  else if (C == 3) FDL_RENDER(3)
+  else FDL_RENDER(4)
+#undef FDL_RENDER
   return cudaGetLastError();
 }
 

@@ -16,6 +16,14 @@ __device__ __forceinline__ void make_twiddles(float2* tw, int L) {
   }
 }
 
+// exp(+i pi k / M), 0 <= k < M, from tw[t] = exp(-2 pi i t / M): conj(tw[k / 2]), times
+// h = exp(i pi / M) for odd k (the twiddle of the real-to-complex split of a length-2M DFT)
+__device__ __forceinline__ float2 half_twiddle_conj(const float2* tw, int k, float2 h) {
+  const float2 t = tw[k >> 1];
+  const float2 c = make_float2(t.x, -t.y);
+  return (k & 1) ? make_float2(c.x * h.x - c.y * h.y, c.x * h.y + c.y * h.x) : c;
+}
+
 template <bool INV>
 __device__ __forceinline__ float2 twid(const float2* tw, int i) {
   float2 w = tw[i];
