@@ -454,7 +454,7 @@ def serving_leg(device, n_requests=2000, rates=(2000.0, 20000.0), budget=2.5e9, 
                     pass
                 next_fid[0] += 1
             # requests go to light fields whose fit has finished (a new one is still fitting)
-            live = [f for f, e in store.entries.items() if e.ready is None or e.ready.query()]
+            live = [f for f in store.entries if store.is_ready(f)]
             r.fid = live[int(picks[r.rid]) % len(live)]
             orig_submit(r)
 
@@ -963,9 +963,9 @@ def main():
     # kernels per step (the ncu launch list of --case step): fit = 2 twiddle tables + rows +
     # cols + exp table + moment check + FP32 solve + 3 selection + 2 double-float solves (one
     # exits at once) + 3 selection + FP64 solve + status = 16; fdl_render = requests + render +
-    # column and row passes = 4; fdl_refocus = gate + 3 fused launches (return at once) +
-    # render + column and row passes = 7
-    launches = 16 + 4 + 7
+    # column and row passes = 4; fdl_refocus = plan + 4 launches of the mixed path (return at
+    # once) + render + column and row passes = 8
+    launches = 16 + 4 + 8
 
     fit_ms = stages["fit_ms"]
     render_ms = stages["render81_ms"] + stages["refocus32_ms"]
@@ -1102,9 +1102,9 @@ def case_render81():
     print(json.dumps({"case": "render81", "shape": list(img.shape)}))
 
 
-def case_fused_mixed():
+def case_mixed_batch():
     """One fdl_refocus launch over 24 requests of three FDLs of 256^2, 512^2 and 1024^2 RGB
-    (N = 16, 30, 40; views, discs and squares), twice: the fused render path."""
+    (N = 16, 30, 40; views, discs and squares), twice: the mixed render path."""
     torch, dev = _case_device()
     import paper_1901_06919_gb300 as F
     from scenes import random_layer_spectra
@@ -1123,7 +1123,7 @@ def case_fused_mixed():
     for _ in range(2):
         F.refocus_specs(specs)
     torch.cuda.synchronize()
-    print(json.dumps({"case": "fused_mixed", "requests": len(specs)}))
+    print(json.dumps({"case": "mixed_batch", "requests": len(specs)}))
 
 
 def case_step():
@@ -1137,7 +1137,7 @@ def case_step():
     print(json.dumps({"case": "step", "tiers": path.F.FitWorkspace.tier_counts(path.ws_fit)}))
 
 
-CASES = {"df512": case_df512, "render81": case_render81, "fused_mixed": case_fused_mixed, "step": case_step}
+CASES = {"df512": case_df512, "render81": case_render81, "mixed_batch": case_mixed_batch, "step": case_step}
 
 
 def measured_hbm():

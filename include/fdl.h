@@ -218,8 +218,8 @@ FDL_API int fdl_fit_tier_counts(const void* workspace, int* counts, void* stream
 /* ---- rendering (Sec. VI-A, Eq. FourierView / Eq. BsFourier) ----------- */
 
 /* B sub-aperture views of one FDL at viewpoints u0 [B][2] (psi = delta):
- * out [B][C][H][W].  Power-of-two sizes up to 2048 rows take the fused
- * render + inverse column DFT of fdl_refocus.  B <= 65535. */
+ * out [B][C][H][W].  The layer values of each tile of frequencies are read
+ * once and shared by the B views.  B <= 65535. */
 FDL_API size_t fdl_render_workspace_size(int B, int C, int H, int W);
 FDL_API int fdl_render(const float* layers, const float* d, int N, int C, int H, int W,
                        const float* u0, int B, float* out, void* workspace,

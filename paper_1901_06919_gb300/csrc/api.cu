@@ -212,13 +212,14 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
 size_t spec_tmp_bytes(int nimg, int H, int W) { return align_up((size_t)nimg * H * (W / 2) * sizeof(float2)); }
 
 // header (counters and status word), [requests], spectra (split main part; the slots of the
-// fused path), the Nyquist plane and the DFT tables of the other paths
+// mixed path), the Nyquist plane, the DFT tables of the other paths and the mixed path's plan
 size_t render_ws_bytes(int B, int C, int H, int W, bool with_reqs) {
   size_t s = align_up(kHeaderInts * sizeof(int));
   if (with_reqs) s += align_up((size_t)B * sizeof(fdl_request));
   s += align_up((size_t)B * C * H * (W / 2) * sizeof(float2));
   s += align_up((size_t)B * C * H * sizeof(float2));
   s += align_up(inv_table_elems(H, W) * sizeof(float4));
+  s += align_up(render_plan_ints(B) * sizeof(int));
   return s;
 }
 
@@ -254,6 +255,7 @@ struct RenderWs {
   float2* main;
   float2* nyq;
   float4* tables;
+  int* plan;  // the mixed path's request groups (launch_render_plan)
 };
 RenderWs carve_render(void* ws, int B, int C, int H, int W, bool with_reqs) {
   Carver cv(ws);
@@ -263,6 +265,7 @@ RenderWs carve_render(void* ws, int B, int C, int H, int W, bool with_reqs) {
   r.main = cv.take<float2>((size_t)B * C * H * (W / 2));
   r.nyq = cv.take<float2>((size_t)B * C * H);
   r.tables = cv.take<float4>(inv_table_elems(H, W));
+  r.plan = cv.take<int>(render_plan_ints(B));
   return r;
 }
 
@@ -270,19 +273,21 @@ RenderWs carve_render(void* ws, int B, int C, int H, int W, bool with_reqs) {
 //  * tiled: spectra of exactly H x W x C with the layer values of each tile of frequencies
 //    staged once and reused by every request of one FDL, then the separate inverse DFT
 //    passes; the only path for sizes that are not powers of two, H = 4096 and per-layer shifts;
-//  * fused: Eq. BsFourier straight into the inverse column DFT, requests of any power-of-two
-//    sizes within (C, H, W) and of different FDLs in one launch.
-// mixed = true (fdl_refocus): a one-CTA check on the device sets the gate word to 1 when the
-// active requests all read one FDL of exactly H x W x C (the tiled path reuses its layers
-// across them), else 0; both paths are enqueued and the one the gate rules out returns at once.
+//  * mixed: requests of any power-of-two sizes within (C, H, W) and of different FDLs in one
+//    launch, the layer values staged once per run of consecutive requests of one FDL, each
+//    request's spectrum in its own slot, then per-request inverse DFT passes.
+// mixed = true (fdl_refocus): a one-CTA kernel on the device sets the gate word to 1 when the
+// active requests all read one FDL of exactly H x W x C (the tiled path), else 0, and plans the
+// request groups of the mixed path; both paths are enqueued and the one the gate rules out
+// returns at once.
 cudaError_t render_requests(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
                             const RenderWs& w, cudaStream_t st, bool mixed, const float* shifts = nullptr) {
   int* status = w.header + kStatusWord;
   const int* gate = nullptr;
-  if (mixed && shifts == nullptr && render_fused_supported(H, W)) {
+  if (mixed && shifts == nullptr && render_mixed_supported(H, W)) {
     int* g = w.header + kGateWord;
-    cudaError_t e = launch_render_gate(req, B, count, C, H, W, Nmax, g, st);
-    if (e == cudaSuccess) e = launch_render_fused(req, B, count, C, H, W, Nmax, w.main, status, st, g);
+    cudaError_t e = launch_render_plan(req, B, count, C, H, W, Nmax, g, w.plan, st);
+    if (e == cudaSuccess) e = launch_render_mixed(req, B, count, C, H, W, Nmax, w.main, w.nyq, w.plan, status, st, g);
     if (e != cudaSuccess) return e;
     gate = g;
   }

@@ -124,7 +124,7 @@ cudaError_t launch_gen_rows_inv(SpecView in, float* out, long long nrows, int H,
 // A render request the kernels can serve: non-null, aligned FDL and output, 1 <= N <= Nmax <= 64,
 // a known aperture, finite parameters, and an image size within (C, H, W): equal to it
 // (exact: the general-length and fixed-size DFT paths) or any power-of-two size of at
-// least 16 within it (the fused power-of-two path).  Requests that fail are skipped
+// least 16 within it (the mixed power-of-two path).  Requests that fail are skipped
 // and set FDL_ST_BAD_REQUEST.
 __device__ __forceinline__ bool request_ok(const fdl_request& r, int C, int H, int W, int Nmax, bool exact) {
   if (r.layers == nullptr || r.d == nullptr || r.out == nullptr) return false;
@@ -152,7 +152,7 @@ constexpr int kHeaderInts = 16;
 // solves form A_jk = P_k^{u_x} Q_k^{u_y} from per-frequency powers.
 constexpr int kLatMax = 4;
 constexpr int kStatusWord = 15;
-constexpr int kGateWord = 14;  // renders: 1 = the tiled path serves the batch, 0 = the fused path
+constexpr int kGateWord = 14;  // renders: 1 = the tiled path serves the batch, 0 = the mixed path
 
 // ---- tier selection (select.cu) ---------------------------------------------
 // sets the status word of a fit from its breakdown and non-finite counters
@@ -172,26 +172,31 @@ cudaError_t launch_select_budget(const float* err, const float* xn2, int n, doub
 cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
                                   SpecView out, int* status, cudaStream_t st, const float* shifts = nullptr,
                                   const int* gate = nullptr);
-// *gate = 1 when every active request is valid, reads the same FDL (layers, d, N) and has
-// exactly the size (C, H, W): the tiled path (layer values staged once per tile of
-// frequencies and reused by every request) serves it; otherwise 0 and the fused path does.
-cudaError_t launch_render_gate(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                               int* gate, cudaStream_t st);
+// One CTA: *gate = 1 when every active request is valid, reads the same FDL (layers, d, N)
+// and has exactly the size (C, H, W): the tiled path (layer values staged once per tile of
+// frequencies and reused by every request) serves it; otherwise 0 and the mixed path does,
+// from `plan` (render_plan_ints(B) ints): the runs of consecutive valid requests of one FDL
+// and their work items (tiles of 32 frequencies).
+size_t render_plan_ints(int B);
+cudaError_t launch_render_plan(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                               int* gate, int* plan, cudaStream_t st);
 // drawn aperture: centred zero-padded raster and its sum (double), then the table scaling
 cudaError_t launch_aperture_table_prep(const float* R, int P, int Z, float* pad, double* sum, cudaStream_t st);
 cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cudaStream_t st);
 cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const float* d, int N, int C, int H,
                                     int W, const float* u0, int B, float* out, cudaStream_t st);
-// Fused render of power-of-two sizes up to 2048 x 4096 (requests of different sizes
-// within (C, H, W) may share the launch): Eq. BsFourier evaluated for a strip of columns
-// straight into shared memory, the inverse column DFT there, the strip written to
-// request b's slot of `slots` (split layout, pitch W_b/2, slot_elems complex per
-// request); then the inverse row DFT from the slots into the requests' outputs.
-bool render_fused_supported(int H, int W);
-size_t render_fused_slot_elems(int C, int H, int W);
+// Mixed render of power-of-two sizes up to 2048 x 4096 (requests of different FDLs and
+// sizes within (C, H, W) in one launch): each plan group's layer values staged per tile of
+// frequencies and rendered for every request of the group into its slot of `slots` (split
+// layout of the request's size, pitch W_b/2, slot_elems complex per request; kx = W_b/2 to
+// nyq[(b C + c) H + ky]), then the inverse column DFT of each request in place and the row
+// DFT into the requests' outputs.
+bool render_mixed_supported(int H, int W);
+size_t render_mixed_slot_elems(int C, int H, int W);
 // gate (nullable, device): returns at once when *gate != 0.
-cudaError_t launch_render_fused(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                                float2* slots, int* status, cudaStream_t st, const int* gate = nullptr);
+cudaError_t launch_render_mixed(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                                float2* slots, float2* nyq, const int* plan, int* status, cudaStream_t st,
+                                const int* gate = nullptr);
 
 // ---- calibration (calib.cu) -------------------------------------------------
 struct CalibParams {

@@ -4,6 +4,8 @@
 // written per request into the split half-spectrum layout, ready for the
 // inverse column and row DFT passes.  psi is normalised to integrate to 1,
 // so psi_hat(0) = 1 and a pinhole (psi = delta) gives psi_hat = 1 (Sec. IV-B).
+#include <algorithm>
+
 #include "hp_solve.cuh"
 #include "stockham.cuh"
 
@@ -188,16 +190,19 @@ __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int k
 #undef FDL_AP
 }
 
-// Two requests on the layer values staged in shared memory, pinhole (AP 0) or disc (AP 1), no
-// shift model: one pass over the layers loads each layer value once for both and keeps two
-// independent chains of phase, aperture and sums in flight.
-template <int CC, int AP>
+// Two requests of one FDL, pinhole (AP 0) or disc (AP 1), no shift model: one pass over the
+// layers loads each layer value once for both (from the shared tile when TILE, else from
+// global memory at plane stride) and keeps two independent chains of phase, aperture and sums
+// in flight.
+template <int CC, int AP, bool TILE = true>
 __device__ __forceinline__ void render_pair(const fdl_request& r1, const fdl_request& r2, int C, df th1, df th2,
                                             float wabs, bool valid, const float2* tile, const float* dsh, int lane,
-                                            float2 acc1[4], float2 acc2[4]) {
+                                            float2 acc1[4], float2 acc2[4], long long plane = 0,
+                                            long long off = 0) {
   const float z1 = 6.283185307f * r1.radius * wabs, z2 = 6.283185307f * r2.radius * wabs;
+  const float2* x = reinterpret_cast<const float2*>(r1.layers);
   for (int k = 0; k < r1.N; ++k) {
-    const float dk = dsh[k];
+    const float dk = TILE ? dsh[k] : __ldg(r1.d + k);
     float2 c1, c2;
     __sincosf(6.28318531f * phase_from_theta(th1, dk), &c1.y, &c1.x);
     __sincosf(6.28318531f * phase_from_theta(th2, dk), &c2.y, &c2.x);
@@ -209,7 +214,7 @@ __device__ __forceinline__ void render_pair(const fdl_request& r1, const fdl_req
 #pragma unroll
       for (int c = 0; c < CC; ++c) {
         if (CC < 4 || c < C) {
-          const float2 v = tile[(k * C + c) * 32 + lane];
+          const float2 v = TILE ? tile[(k * C + c) * 32 + lane] : __ldg(x + ((long long)k * C + c) * plane + off);
           cfma(acc1[c], c1, v);
           cfma(acc2[c], c2, v);
         }
@@ -361,13 +366,147 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   }
 }
 
+// Work-item span (frequencies) of a group of nb requests in the mixed render: 32 (one per lane,
+// the layer values staged once for the 8 warps) from 8 requests on, else 256 (one tile of 32
+// per warp, the layer values read once per warp for its nb requests).
+__host__ __device__ __forceinline__ int grp_span(int nb) { return nb >= kRenderWarps ? 32 : 32 * kRenderWarps; }
+
+// Mixed path, render: work item w of the plan is tile t of group g.  Groups of 8 requests or
+// more: the CTA stages the group's layer values of 32 frequencies in shared memory once and the
+// warps take the requests (two at a time where render_pair applies).  Smaller groups: each warp
+// takes 32 frequencies of a 256-frequency tile and renders every request of the group there,
+// reading each layer value once from global memory for all of them.  Request b's spectrum goes
+// to its slot in the split layout of its own size (pitch M_b = W_b/2; kx = W_b/2 to
+// nyq[(b Cmax + c) Hmax + ky]).  A persistent grid strides over the work items.
+template <int CC>
+__global__ void __launch_bounds__(kRenderWarps * 32) k_render_grp(const fdl_request* __restrict__ req, int B,
+                                                                  int Cmax, int Hmax, const int* __restrict__ plan,
+                                                                  float2* __restrict__ slots, long long slot_elems,
+                                                                  float2* __restrict__ nyq,
+                                                                  const int* __restrict__ gate) {
+  extern __shared__ float2 tile[];  // [N C][32]
+  __shared__ float dsh[64];
+  if (gate != nullptr && *gate != 0) return;
+  const int ng = plan[0], total = plan[1];
+  const int* gstart = plan + 2;
+  const int* gcount = gstart + B;
+  const int* gprefix = gcount + B;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    int lo = 0, hi = ng - 1;  // the last group starting at or before w
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (gprefix[mid] <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    const int b0 = gstart[lo], nb = gcount[lo];
+    const int t = w - gprefix[lo];
+    const bool staged = nb >= kRenderWarps;
+    const fdl_request r0 = req[b0];
+    const int H = r0.H, W = r0.W, C = r0.C, N = r0.N, M = W >> 1;
+    const int Qs = H * (M + 1);
+    const int q = t * grp_span(nb) + (staged ? 0 : 32 * warp) + lane;
+    const bool valid = q < Qs;
+    int ky, kx;
+    bin_coords(valid ? q : 0, H, M, ky, kx);
+    const Freq fq = bin_freq(ky, kx, H, W);
+    const float wy = fq.wy, wx = fq.wx;
+    const float wabs = sqrtf(wx * wx + wy * wy);
+    const long long plane = (long long)H * (M + 1);
+    const long long off = (long long)ky * (M + 1) + kx;
+    auto put = [&](int b, const float2* a) {
+      float2* sl = slots + (long long)b * slot_elems;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < C) {
+          if (kx < M) sl[((long long)c * H + ky) * M + kx] = a[c];
+          else nyq[((long long)b * Cmax + c) * Hmax + ky] = a[c];
+        }
+      }
+    };
+    auto theta_of = [&](const fdl_request& r) {
+      return df_add_f(df_add(two_prod(r.u0x, wx), two_prod(r.u0y, wy)), fmaf(r.u0x, fq.wx_lo, r.u0y * fq.wy_lo));
+    };
+    if (staged) {
+      __syncthreads();  // the previous staged work item's reads of tile and dsh are done
+      const float2* x0 = reinterpret_cast<const float2*>(r0.layers);
+      for (int e = threadIdx.x; e < N * C * 32; e += blockDim.x) {
+        const int lc = e >> 5, l2 = e & 31;
+        const int qq = t * 32 + l2;
+        float2 v = make_float2(0.f, 0.f);
+        if (qq < Qs) {
+          int yy, xx;
+          bin_coords(qq, H, M, yy, xx);
+          v = __ldg(x0 + (long long)lc * plane + (long long)yy * (M + 1) + xx);
+        }
+        tile[e] = v;
+      }
+      for (int k = threadIdx.x; k < N; k += blockDim.x) dsh[k] = __ldg(r0.d + k);
+      __syncthreads();
+    } else if (q - lane >= Qs) {
+      continue;  // this warp's 32 frequencies lie past the image
+    }
+    // requests bi = first, first + step, ...: the warps over the requests (staged), or every
+    // request in each warp
+    const int first = staged ? warp : 0, step = staged ? kRenderWarps : 1;
+    for (int bi = first; bi < nb; bi += step) {
+      const fdl_request r = req[b0 + bi];
+      const df theta = theta_of(r);
+      const int bi2 = bi + step;
+      if (bi2 < nb) {
+        const fdl_request r2 = req[b0 + bi2];
+        const int k1 = pair_class(r), k2 = pair_class(r2);
+        if (k1 >= 0 && k1 == k2) {
+          float2 a1[4], a2[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) a1[c] = a2[c] = make_float2(0.f, 0.f);
+          const df th2 = theta_of(r2);
+          if (staged) {
+            if (k1 == 0) render_pair<CC, 0, true>(r, r2, C, theta, th2, wabs, valid, tile, dsh, lane, a1, a2);
+            else render_pair<CC, 1, true>(r, r2, C, theta, th2, wabs, valid, tile, dsh, lane, a1, a2);
+          } else {
+            if (k1 == 0)
+              render_pair<CC, 0, false>(r, r2, C, theta, th2, wabs, valid, nullptr, nullptr, lane, a1, a2, plane, off);
+            else
+              render_pair<CC, 1, false>(r, r2, C, theta, th2, wabs, valid, nullptr, nullptr, lane, a1, a2, plane, off);
+          }
+          if (valid) {
+            put(b0 + bi, a1);
+            put(b0 + bi2, a2);
+          }
+          bi = bi2;
+          continue;
+        }
+      }
+      float2 acc[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+      render_terms<CC>(r, 0, 1, C, theta, wy, wx, wabs, plane, off, valid, staged ? tile : nullptr, dsh, lane, acc,
+                       nullptr, fq);
+      if (valid) put(b0 + bi, acc);
+    }
+  }
+}
+
+__device__ __forceinline__ bool same_fdl(const fdl_request& a, const fdl_request& b) {
+  return a.layers == b.layers && a.d == b.d && a.N == b.N && a.H == b.H && a.W == b.W && a.C == b.C;
+}
+
 // *gate = 1 when every active request passes request_ok with exactly (C, H, W) and reads the
-// same FDL (layers, d, N) as request 0, else 0.
-__global__ void __launch_bounds__(256) k_render_gate(const fdl_request* __restrict__ req, int B,
+// same FDL (layers, d, N) as request 0 (the tiled path), else 0.  plan = [ngroups, tiles,
+// gstart[B], gcount[B], gprefix[B + 1]]: the groups of the mixed path, runs of consecutive
+// valid requests of one FDL (same layers, d, N and size), group g covering work items
+// [gprefix[g], gprefix[g + 1]), one per tile of grp_span(gcount[g]) of its H (W/2 + 1)
+// frequencies.
+__global__ void __launch_bounds__(256) k_render_plan(const fdl_request* __restrict__ req, int B,
                                                      const int* __restrict__ count, int C, int H, int W, int Nmax,
-                                                     int* __restrict__ gate) {
+                                                     int* __restrict__ gate, int* __restrict__ plan) {
   __shared__ int ok;
+  int* gstart = plan + 2;
+  int* gcount = gstart + B;
+  int* gprefix = gcount + B;
   if (threadIdx.x == 0) ok = 1;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) gcount[i] = 0;
   __syncthreads();
   const int Bact = count ? min(*count, B) : B;
   for (int b = threadIdx.x; b < Bact; b += blockDim.x) {
@@ -376,6 +515,50 @@ __global__ void __launch_bounds__(256) k_render_gate(const fdl_request* __restri
       ok = 0;
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    // group ids by a ballot over chunks of 32 requests: a valid request starts a group unless
+    // the request before it is valid and reads the same FDL
+    int ng = 0;
+    for (int i0 = 0; i0 < Bact; i0 += 32) {
+      const int i = i0 + lane;
+      bool v = false, st = false;
+      if (i < Bact) {
+        v = request_ok(req[i], C, H, W, Nmax, false);
+        st = v && !(i > 0 && request_ok(req[i - 1], C, H, W, Nmax, false) && same_fdl(req[i - 1], req[i]));
+      }
+      const unsigned starts = __ballot_sync(0xffffffffu, st);
+      const int gid = ng + __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+      if (st) gstart[gid] = i;
+      if (v) atomicAdd(gcount + gid, 1);
+      ng += __popc(starts);
+    }
+    __syncwarp();
+    // work items: an exclusive scan of the groups' tile counts
+    int acc = 0;
+    for (int g0 = 0; g0 < ng; g0 += 32) {
+      const int g = g0 + lane;
+      int t = 0;
+      if (g < ng) {
+        const fdl_request& r = req[gstart[g]];
+        const int span = grp_span(gcount[g]);
+        t = (r.H * (r.W / 2 + 1) + span - 1) / span;
+      }
+      int x = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (g < ng) gprefix[g] = acc + x - t;
+      acc += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) {
+      gprefix[ng] = acc;
+      plan[0] = ng;
+      plan[1] = acc;
+    }
+  }
   if (threadIdx.x == 0) *gate = ok;
 }
 
@@ -437,12 +620,13 @@ __global__ void k_scale_table(float2* __restrict__ T, long long n, const double*
     T[e] = make_float2(T[e].x * inv, T[e].y * inv);
 }
 
-// ------------------------------------------------------------ fused power-of-two path
-// One CTA renders a strip of SW columns of one request's half spectrum (all H rows) by
-// Eq. BsFourier straight into shared memory, runs the inverse DFT along y there and
-// writes the strip in the split layout of the row pass: the rendered spectrum itself
-// never reaches HBM.  Requests of different power-of-two sizes share a launch: each CTA
-// takes its request's H, W, C, N from the descriptor (grid sized for the largest).
+// ------------------------------------------------------------ mixed power-of-two path
+// Requests of different FDLs and power-of-two sizes in one launch: k_render_grp writes each
+// request's rendered half spectrum into its slot (split layout of its own size); a CTA of
+// k_cols_req then takes a strip of SW columns of one request (all H rows) into shared memory,
+// runs the inverse DFT along y there and writes the strip back in place; k_irfft_rows_req
+// finishes the rows.  Every CTA reads its request's sizes from the descriptor (grids sized
+// for the largest).
 constexpr int kRcThreads = 256;
 constexpr int kRcFreqs = 2048;  // H * SW of a CTA's strip (the strip of one column when H > 2048 is not used)
 constexpr int kRcMaxH = 2048;
@@ -457,79 +641,17 @@ __host__ __device__ __forceinline__ int rc_strip(int H, int M) {
 
 __device__ __forceinline__ int log2_pow2(int v) { return 31 - __clz(v); }
 
-// Terms of Eq. BsFourier over the layers at one frequency: acc[c] += exp(+2 pi i d_k (u0 . w))
-// psi_hat((s - d_k) w) x_kc(w).  REC (disparities on a grid d_k = d_0 + k delta, deviations
-// within the check of the caller): the phase factor advances by exp(2 pi i delta (u0 . w))
-// from layer to layer and is evaluated directly every 8 layers; otherwise it is evaluated
-// at every layer.  AP as in render_terms_t.
-template <int AP, bool REC>
-__device__ __forceinline__ void rc_layers(const fdl_request& r, const float* dsh, float delta, int N, int C,
-                                          const float2* __restrict__ x, long long plane, long long off, df theta,
-                                          float wy, float wx, float wabs, float2 acc[4]) {
-  float2 step = make_float2(1.f, 0.f), cur = make_float2(1.f, 0.f);
-  if (REC) {
-    float sn, cs;
-    sincospif(2.f * phase_from_theta(theta, delta), &sn, &cs);
-    step = make_float2(cs, sn);
-  }
-  const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
-#pragma unroll 4
-  for (int k = 0; k < N; ++k) {
-    const float dk = dsh[k];
-    // |2 pi ph| <= pi: the hardware sine and cosine (absolute error about 2^-21 there)
-    if (!REC || (k & 7) == 0) __sincosf(6.28318531f * phase_from_theta(theta, dk), &cur.y, &cur.x);
-    float2 coef = cur;
-    if constexpr (AP == 1) {
-      coef = cscale(coef, disc_hat(zscale * fabsf(r.s - dk)));
-    } else if constexpr (AP == 2) {
-      const float sd = r.s - dk;
-      coef = cmul(coef, aperture_table_hat(reinterpret_cast<const float2*>(r.pts), r.npts, r.radius, sd * wy, sd * wx));
-    } else if constexpr (AP == 3) {
-      const float sd = r.s - dk;
-      coef = cmul(coef, aperture_hat(r.aperture, r.radius, r.pts, r.npts, sd * wy, sd * wx));
-    }
-    const float2* xk = x + (long long)k * C * plane + off;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (c < C) cfma(acc[c], coef, __ldg(xk + (long long)c * plane));
-    if (REC) cur = cmul(cur, step);
-  }
-}
-
-__device__ __forceinline__ void rc_render_freq(const fdl_request& r, int ap, bool rec, const float* dsh, float delta,
-                                               int N, int C, const float2* __restrict__ x, long long plane,
-                                               long long off, df theta, float wy, float wx, float wabs,
-                                               float2 acc[4]) {
-#define FDL_RC(A, RE) rc_layers<A, RE>(r, dsh, delta, N, C, x, plane, off, theta, wy, wx, wabs, acc)
-  if (rec) {
-    if (ap == 0) FDL_RC(0, true);
-    else if (ap == 1) FDL_RC(1, true);
-    else if (ap == 2) FDL_RC(2, true);
-    else FDL_RC(3, true);
-  } else {
-    if (ap == 0) FDL_RC(0, false);
-    else if (ap == 1) FDL_RC(1, false);
-    else if (ap == 2) FDL_RC(2, false);
-    else FDL_RC(3, false);
-  }
-#undef FDL_RC
-}
-
-// FIRST: column 0 and the Nyquist column kx = W/2 of every request, packed as Herm(F0) +
-// i Herm(FN) before the inverse DFT (the split layout's element 0 of each row); otherwise
-// strip blockIdx.y of SW columns (column 0 of strip 0 is left to the FIRST launch).
-// Request b = blockIdx.x, so consecutive CTAs render the same strip of different requests
-// and the layer values of the strip stay in L2 between them.
+// FIRST: column 0 and the Nyquist column kx = W/2 of every request (from nyq), packed as
+// Herm(F0) + i Herm(FN) before the inverse DFT (the split layout's element 0 of each row);
+// otherwise strip blockIdx.y of SW columns (column 0 of strip 0 is left to the FIRST launch,
+// which runs after this one).  Request b = blockIdx.x.
 template <bool FIRST>
-__global__ void __launch_bounds__(kRcThreads) k_render_cols(const fdl_request* __restrict__ req,
-                                                            const int* __restrict__ count, int Cmax, int Hmax,
-                                                            int Wmax, int Nmax, float2* __restrict__ slots,
-                                                            long long slot_elems, int* __restrict__ status,
-                                                            const int* __restrict__ gate) {
+__global__ void __launch_bounds__(kRcThreads) k_cols_req(const fdl_request* __restrict__ req,
+                                                         const int* __restrict__ count, int Cmax, int Hmax, int Wmax,
+                                                         int Nmax, float2* __restrict__ slots, long long slot_elems,
+                                                         const float2* __restrict__ nyqp, int* __restrict__ status,
+                                                         const int* __restrict__ gate) {
   extern __shared__ float2 sm[];
-  __shared__ float dsh[64];
-  __shared__ float sdelta;
-  __shared__ int srec;
   const int b = blockIdx.x;
   if (gate != nullptr && *gate != 0) return;
   if (count != nullptr && b >= *count) return;
@@ -538,7 +660,7 @@ __global__ void __launch_bounds__(kRcThreads) k_render_cols(const fdl_request* _
     if (FIRST && threadIdx.x == 0) atomicOr(status, FDL_ST_BAD_REQUEST);
     return;
   }
-  const int H = r.H, W = r.W, C = r.C, N = r.N, M = W >> 1;
+  const int H = r.H, W = r.W, C = r.C, M = W >> 1;
   const int SW = FIRST ? 1 : rc_strip(H, M);
   const int c0 = FIRST ? 0 : (int)blockIdx.y * SW;
   if (c0 >= M) return;
@@ -547,64 +669,24 @@ __global__ void __launch_bounds__(kRcThreads) k_render_cols(const fdl_request* _
   float2* tw = sm;           // [H]
   float2* data = sm + Hmax;  // [C][H][SW]
   float2* nyq = data + (long long)Cmax * Hmax;  // FIRST: [C][H], the Nyquist column
-  for (int k = threadIdx.x; k < N; k += blockDim.x) dsh[k] = __ldg(r.d + k);
   make_twiddles(tw, H);
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    // the grid the recurrence follows and the largest deviation from it
-    const float delta = N > 1 ? (dsh[N - 1] - dsh[0]) / (float)(N - 1) : 0.f;
-    float em = 0.f;
-    for (int k = threadIdx.x; k < N; k += 32)
-      em = fmaxf(em, fabsf((float)((double)dsh[k] - (double)dsh[0] - (double)k * (double)delta)));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
-    if (threadIdx.x == 0) {
-      // |w_x|, |w_y| <= 1/2: the phase of the factor drifts from the exact one by at most
-      // 2 pi (2 em) (|u0x| + |u0y|) / 2 between two direct evaluations
-      const float drift = 6.2831853f * em * (fabsf(r.u0x) + fabsf(r.u0y));
-      sdelta = delta;
-      srec = (N >= 2 && isfinite(delta) && drift <= 2e-6f) ? 1 : 0;
-    }
-  }
-  __syncthreads();
-  const float delta = sdelta;
-  const bool rec = srec != 0;
-  const int ap = (r.aperture == FDL_AP_PINHOLE || (r.aperture == FDL_AP_DISC && r.radius == 0.f)) ? 0
-                 : r.aperture == FDL_AP_DISC                                                  ? 1
-                 : r.aperture == FDL_AP_TABLE                                                 ? 2
-                                                                                              : 3;
-  const float2* x = reinterpret_cast<const float2*>(r.layers);
-  const long long plane = (long long)H * (M + 1);
+  float2* slot = slots + (long long)b * slot_elems;
   const int nf = FIRST ? 2 * H : HS;
   for (int f = threadIdx.x; f < nf; f += blockDim.x) {
-    int ky, kx;
     if (FIRST) {
-      ky = f < H ? f : f - H;
-      kx = f < H ? 0 : M;
-    } else {
-      ky = f >> logSW;
-      kx = c0 + (f & (SW - 1));
-    }
-    float2 acc[4];
+      const int ky = f < H ? f : f - H;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
-    if (FIRST || kx != 0) {
-      const Freq fq = bin_freq(ky, kx, H, W);
-      const df theta =
-          df_add_f(df_add(two_prod(r.u0x, fq.wx), two_prod(r.u0y, fq.wy)), fmaf(r.u0x, fq.wx_lo, r.u0y * fq.wy_lo));
-      const float wabs = sqrtf(fq.wx * fq.wx + fq.wy * fq.wy);
-      rc_render_freq(r, ap, rec, dsh, delta, N, C, x, plane, (long long)ky * (M + 1) + kx, theta, fq.wy, fq.wx, wabs,
-                     acc);
-    }
-    if (FIRST) {
-      float2* dst = f < H ? data + ky : nyq + ky;
+      for (int c = 0; c < 4; ++c) {
+        if (c < C) {
+          if (f < H) data[c * H + ky] = slot[((long long)c * H + ky) * M];
+          else nyq[c * H + ky] = nyqp[((long long)b * Cmax + c) * Hmax + ky];
+        }
+      }
+    } else {
+      const int ky = f >> logSW, kx = c0 + (f & (SW - 1));
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        if (c < C) dst[c * H] = acc[c];
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (c < C) data[c * HS + f] = acc[c];
+        if (c < C) data[c * HS + f] = slot[((long long)c * H + ky) * M + kx];
     }
   }
   __syncthreads();
@@ -635,17 +717,16 @@ __global__ void __launch_bounds__(kRcThreads) k_render_cols(const fdl_request* _
     }
   }
   for (int c = 0; c < C; ++c) stockham<true, 2>(data + c * HS, tw, H, logH, SW, logSW, 1, SW);
-  float2* dst = slots + (long long)b * slot_elems;
   for (int f = threadIdx.x; f < HS; f += blockDim.x) {
     const int ky = f >> logSW, kx = c0 + (f & (SW - 1));
     if (!FIRST && kx == 0) continue;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      if (c < C) dst[((long long)c * H + ky) * M + kx] = data[c * HS + f];
+      if (c < C) slot[((long long)c * H + ky) * M + kx] = data[c * HS + f];
   }
 }
 
-// Inverse row DFT of the fused path: rows of request b's slot (pitch M = W_b/2, element 0
+// Inverse row DFT of the mixed path: rows of request b's slot (pitch M = W_b/2, element 0
 // packing X[0] + i X[W/2]) -> the request's output, times 1 / (H W).  A CTA takes
 // kRcFreqs / M consecutive rows of one request.
 __global__ void __launch_bounds__(kRcThreads) k_irfft_rows_req(const fdl_request* __restrict__ req,
@@ -731,9 +812,11 @@ cudaError_t launch_aperture_table_scale(float2* T, int Z, const double* sum, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_render_gate(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                               int* gate, cudaStream_t st) {
-  k_render_gate<<<1, 256, 0, st>>>(req, B, count, C, H, W, Nmax, gate);
+size_t render_plan_ints(int B) { return 3 * (size_t)B + 3; }
+
+cudaError_t launch_render_plan(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                               int* gate, int* plan, cudaStream_t st) {
+  k_render_plan<<<1, 256, 0, st>>>(req, B, count, C, H, W, Nmax, gate, plan);
   return cudaGetLastError();
 }
 
@@ -764,31 +847,44 @@ cudaError_t launch_pinhole_requests(fdl_request* req, const float* layers, const
   return cudaGetLastError();
 }
 
-bool render_fused_supported(int H, int W) {
+bool render_mixed_supported(int H, int W) {
   auto p2 = [](int v) { return v >= 16 && (v & (v - 1)) == 0; };
   return p2(H) && p2(W) && H <= kRcMaxH && W <= 4096;
 }
 
-size_t render_fused_slot_elems(int C, int H, int W) { return (size_t)C * H * (W / 2); }
+size_t render_mixed_slot_elems(int C, int H, int W) { return (size_t)C * H * (W / 2); }
 
-cudaError_t launch_render_fused(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
-                                float2* slots, int* status, cudaStream_t st, const int* gate) {
-  if (!render_fused_supported(H, W) || B < 1 || B > 65535) return cudaErrorInvalidValue;
-  const long long se = (long long)render_fused_slot_elems(C, H, W);
+cudaError_t launch_render_mixed(const fdl_request* req, int B, const int* count, int C, int H, int W, int Nmax,
+                                float2* slots, float2* nyq, const int* plan, int* status, cudaStream_t st,
+                                const int* gate) {
+  if (!render_mixed_supported(H, W) || B < 1 || B > 65535 || Nmax < 1 || Nmax > 64 || C < 1 || C > 4)
+    return cudaErrorInvalidValue;
+  const long long se = (long long)render_mixed_slot_elems(C, H, W);
   const int M = W / 2;
-  // a request within (C, H, W) has at most as many strips and row blocks as one of that size
+  // render: a persistent grid over the plan's work items (at most B tiles of the largest size)
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long items = (long long)B * (((long long)H * (M + 1) + 31) / 32);
+  const int grid_r = (int)std::min<long long>(items, (long long)(sms > 0 ? sms : 148) * 12);
+  const size_t smem_r = (size_t)Nmax * C * 32 * sizeof(float2);
+  // inverse column pass: a request within (C, H, W) has at most as many strips and row blocks
+  // as one of that size
   const int strips = M / rc_strip(H, M);
   const long long row_blocks = ((long long)C * H * M + kRcFreqs - 1) / kRcFreqs;
   const size_t smem_main = (size_t)(H + (size_t)C * (H > kRcFreqs ? H : kRcFreqs)) * sizeof(float2);
   const size_t smem_first = (size_t)(H + 2 * (size_t)C * H) * sizeof(float2);
   const size_t smem_rows = (size_t)(M + kRcFreqs) * sizeof(float2);
-  cudaError_t e = set_smem((const void*)k_render_cols<false>, smem_main);
-  if (e == cudaSuccess) e = set_smem((const void*)k_render_cols<true>, smem_first);
+  e = set_smem((const void*)k_render_grp<4>, smem_r);
+  if (e == cudaSuccess) e = set_smem((const void*)k_cols_req<false>, smem_main);
+  if (e == cudaSuccess) e = set_smem((const void*)k_cols_req<true>, smem_first);
   if (e == cudaSuccess) e = set_smem((const void*)k_irfft_rows_req, smem_rows);
   if (e != cudaSuccess) return e;
-  k_render_cols<false><<<dim3(B, strips), kRcThreads, smem_main, st>>>(req, count, C, H, W, Nmax, slots, se, status,
-                                                                        gate);
-  k_render_cols<true><<<dim3(B, 1), kRcThreads, smem_first, st>>>(req, count, C, H, W, Nmax, slots, se, status, gate);
+  k_render_grp<4><<<grid_r, kRenderWarps * 32, smem_r, st>>>(req, B, C, H, plan, slots, se, nyq, gate);
+  k_cols_req<false><<<dim3(B, strips), kRcThreads, smem_main, st>>>(req, count, C, H, W, Nmax, slots, se, nyq, status,
+                                                                    gate);
+  k_cols_req<true><<<dim3(B, 1), kRcThreads, smem_first, st>>>(req, count, C, H, W, Nmax, slots, se, nyq, status, gate);
   k_irfft_rows_req<<<dim3((unsigned)row_blocks, B), kRcThreads, smem_rows, st>>>(req, count, C, H, W, Nmax, slots,
                                                                                  se, gate);
   return cudaGetLastError();

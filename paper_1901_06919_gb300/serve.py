@@ -120,6 +120,14 @@ class FdlStore:
         e.last_used = time.perf_counter()
         return e
 
+    def is_ready(self, fid: int) -> bool:
+        """True once the FDL's fit has finished on the device (its event is then dropped, so
+        later calls cost nothing and batches no longer wait on it)."""
+        e = self.entries[fid]
+        if e.ready is not None and e.ready.query():
+            e.ready = None
+        return e.ready is None
+
 
 @dataclass
 class Request:
@@ -173,8 +181,8 @@ class _Batch:
         self.stream.synchronize()
 
     def launch(self, reqs: list[Request], store: FdlStore, pts: dict, batch_id: int = -1, timeline=None):
-        # requests of one FDL side by side: the fused render's consecutive CTAs then read the
-        # same strip of layer values, which stays in L2 between them
+        # requests of one FDL side by side: the mixed render stages each FDL's layer values
+        # once per run of consecutive requests that read it
         reqs = sorted(reqs, key=lambda r: r.fid)
         arr = (L.Request * self.cap).from_buffer(self.host_desc.numpy())
         waits = {}

@@ -1,7 +1,7 @@
 """Requests of different image sizes in one render launch, and the device status word.
 
 * fdl_refocus takes requests of any power-of-two sizes (and channel counts) within its
-  (C, H, W) bounds in one launch (the fused render + inverse column DFT path); each image
+  (C, H, W) bounds in one launch (the mixed path: grouped render, per-request inverse DFT); each image
   must match the FP64 oracle's render of its own FDL within the pixel tolerance 1e-4 and the
   same request rendered alone.
 * Requests the kernels reject (they cannot be checked on the host: the descriptors live in
@@ -78,7 +78,7 @@ def test_mixed_image_sizes_in_one_launch(fdl):
 
 @pytest.mark.parametrize("H,W", [(2048, 32), (16, 4096), (16, 16)])
 def test_extreme_aspect_ratios(fdl, H, W):
-    """The fused path at its edges: one column per strip (H = 2048), a 128-column strip and a
+    """The mixed path at its edges: one column per strip (H = 2048), a 128-column strip and a
     single strip per image, next to a small request in the same launch."""
     X = random_layer_spectra(11, 4, 1, H, W)
     d = np.linspace(-1, 1, 4).astype(np.float32)

@@ -57,6 +57,28 @@ def test_allocation_failure_rolls_back():
         st.admit(1, v, u, d)  # duplicate id
 
 
+class _FakeEvent:
+    def __init__(self, done_after):
+        self.n = done_after
+
+    def query(self):
+        self.n -= 1
+        return self.n < 0
+
+
+def test_is_ready_follows_the_fit_event_and_then_forgets_it():
+    st = FdlStore(budget_bytes=FdlStore.fdl_bytes(4, 1, 16, 16), device="cpu")
+    v, u, d = _views()
+    st.admit(1, v, u, d)
+    assert st.is_ready(1)  # no fit on the device: ready at once
+    st.entries[1].ready = ev = _FakeEvent(done_after=2)
+    assert not st.is_ready(1) and not st.is_ready(1)
+    assert st.is_ready(1)
+    assert st.entries[1].ready is None  # dropped: batches no longer wait on it
+    calls = ev.n
+    assert st.is_ready(1) and ev.n == calls  # not queried again
+
+
 class _StuckBatch:
     busy = True
     requests = []
