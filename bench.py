@@ -1103,8 +1103,9 @@ def case_render81():
 
 
 def case_mixed_batch():
-    """One fdl_refocus launch over 24 requests of three FDLs of 256^2, 512^2 and 1024^2 RGB
-    (N = 16, 30, 40; views, discs and squares), twice: the mixed render path."""
+    """fdl_refocus over 24 requests of three FDLs of 256^2, 512^2 and 1024^2 RGB (N = 16, 30, 40;
+    views, discs and squares): twice with the FDLs interleaved (every request its own group of
+    the mixed render), then twice sorted by FDL (groups of 8)."""
     torch, dev = _case_device()
     import paper_1901_06919_gb300 as F
     from scenes import random_layer_spectra
@@ -1120,8 +1121,9 @@ def case_mixed_batch():
         kind = ("pinhole", "disc", "square")[i % 3]
         specs.append(F.RenderSpec(X, dd, tuple(rng.uniform(-4, 4, 2)), float(rng.uniform(-3, 3)), kind,
                                   0.0 if kind == "pinhole" else float(rng.uniform(0.5, 3))))
-    for _ in range(2):
-        F.refocus_specs(specs)
+    ordered = [specs[i] for k in range(3) for i in range(k, 24, 3)]
+    for batch in (specs, specs, ordered, ordered):
+        F.refocus_specs(batch)
     torch.cuda.synchronize()
     print(json.dumps({"case": "mixed_batch", "requests": len(specs)}))
 

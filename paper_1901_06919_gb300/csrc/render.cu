@@ -13,6 +13,19 @@ namespace fdl {
 
 namespace {
 
+// sin(pi x) / (pi x): the Taylor series in (pi x)^2 to the (pi x)^8 term for |x| < 1/4 (first
+// omitted term below 3e-9), else the SFU sine of pi (x - 2 rint(x / 2)) in [-pi, pi] (absolute
+// error about 2^-21 there) over pi x >= pi / 4.
+__device__ __forceinline__ float sinc_pi(float x) {
+  const float px = 3.14159265f * x;
+  if (fabsf(x) < 0.25f) {
+    const float t = px * px;
+    return 1.f + t * (-1.f / 6.f + t * (1.f / 120.f + t * (-1.f / 5040.f + t * (1.f / 362880.f))));
+  }
+  const float xr = fmaf(-2.f, rintf(0.5f * x), x);
+  return __fdividef(__sinf(3.14159265f * xr), px);
+}
+
 // Fourier transform of the aperture at nu = (s - d_k) w (cycles per unit of u).
 __device__ __forceinline__ float2 aperture_hat(int kind, float radius, const float* pts, int npts, float nuy,
                                                float nux) {
@@ -38,10 +51,7 @@ __device__ __forceinline__ float2 aperture_hat(int kind, float radius, const flo
     return make_float2(2.f * j1f(z) / z, 0.f);
   }
   // square of half side r: sinc(2 r nu_x) sinc(2 r nu_y), sinc(x) = sin(pi x) / (pi x)
-  const float sx = 2.f * radius * nux, sy = 2.f * radius * nuy;
-  const float fx = sx == 0.f ? 1.f : sinpif(sx) / (3.14159265358979f * sx);
-  const float fy = sy == 0.f ? 1.f : sinpif(sy) / (3.14159265358979f * sy);
-  return make_float2(fx * fy, 0.f);
+  return make_float2(sinc_pi(2.f * radius * nux) * sinc_pi(2.f * radius * nuy), 0.f);
 }
 
 // psi_hat(nu) of a drawn aperture: bilinear interpolation of the table T (half spectrum
@@ -304,17 +314,10 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   const bool shared = uniform && N0 * C <= tile_lc && N0 <= 64;
   if (shared) {
     const float2* x0 = reinterpret_cast<const float2*>(L0);
-    for (int e = threadIdx.x; e < N0 * C * 32; e += blockDim.x) {
-      const int lc = e >> 5, l2 = e & 31;
-      const int qq = blockIdx.x * 32 + l2;
-      float2 v = make_float2(0.f, 0.f);
-      if (qq < Qs) {
-        int yy, xx;
-        bin_coords(qq, H, M, yy, xx);
-        v = __ldg(x0 + (long long)lc * plane + (long long)yy * (M + 1) + xx);
-      }
-      tile[e] = v;
-    }
+    // element e = (layer, channel) e / 32 at this thread's own frequency (e % 32 = lane: the
+    // block is a multiple of 32 threads)
+    for (int e = threadIdx.x; e < N0 * C * 32; e += blockDim.x)
+      tile[e] = valid ? __ldg(x0 + (long long)(e >> 5) * plane + off) : make_float2(0.f, 0.f);
     for (int k = threadIdx.x; k < N0; k += blockDim.x) dsh[k] = __ldg(req[0].d + k);
     __syncthreads();
   }
@@ -430,17 +433,9 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render_grp(const fdl_requ
     if (staged) {
       __syncthreads();  // the previous staged work item's reads of tile and dsh are done
       const float2* x0 = reinterpret_cast<const float2*>(r0.layers);
-      for (int e = threadIdx.x; e < N * C * 32; e += blockDim.x) {
-        const int lc = e >> 5, l2 = e & 31;
-        const int qq = t * 32 + l2;
-        float2 v = make_float2(0.f, 0.f);
-        if (qq < Qs) {
-          int yy, xx;
-          bin_coords(qq, H, M, yy, xx);
-          v = __ldg(x0 + (long long)lc * plane + (long long)yy * (M + 1) + xx);
-        }
-        tile[e] = v;
-      }
+      // element e = (layer, channel) e / 32 at this thread's own frequency (e % 32 = lane)
+      for (int e = threadIdx.x; e < N * C * 32; e += blockDim.x)
+        tile[e] = valid ? __ldg(x0 + (long long)(e >> 5) * plane + off) : make_float2(0.f, 0.f);
       for (int k = threadIdx.x; k < N; k += blockDim.x) dsh[k] = __ldg(r0.d + k);
       __syncthreads();
     } else if (q - lane >= Qs) {
