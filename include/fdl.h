@@ -242,9 +242,8 @@ FDL_API int fdl_refocus(const fdl_request* req, int B, const int* count, int C, 
                         void* stream);
 
 /* One light field from host memory to host memory: the views (HOST
- * float32 [K][C][H][W]) are read by the forward DFT where they are when they
- * are pinned (mapped into the device's address space; NVLink-C2C on GB300),
- * else copied into the workspace first; fitted into `layers` (DEVICE
+ * float32 [K][C][H][W], pinned for an asynchronous copy) are copied into the
+ * workspace, fitted into `layers` (DEVICE
  * [N][C][H][W/2+1]) as by
  * fdl_fit, the B requests (DEVICE array, as for fdl_refocus with bounds C, H,
  * W and Nmax = N; they read `layers` and write inside `images`) are rendered,
