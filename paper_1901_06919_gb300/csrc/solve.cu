@@ -32,7 +32,7 @@ namespace fdl {
 namespace {
 
 constexpr int kTileBins = 8;    // bins per CTA tile = warps per CTA
-constexpr int kViewChunk = 32;  // views staged per pass
+constexpr int kViewChunk = 128;  // views staged per pass (one pass for K <= 128)
 
 // ------------------------------------------------------------------ FP32
 template <int NMAX>
@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, 
   float2* myA = arow + warp * NMAX;
   float2* myL = Ls + warp * NMAX * (NMAX + 1);
   __shared__ int cnt_local[4];
+  __shared__ float2 ustage[kViewChunk];  // u_j of the staged views
   if (threadIdx.x < 4) cnt_local[threadIdx.x] = 0;
 
   const int Qs = p.H * (M + 1);
@@ -97,35 +98,40 @@ __global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, 
     for (int j0 = 0; j0 < K; j0 += kViewChunk) {
       const int nv = min(kViewChunk, K - j0);
       __syncthreads();
-      // stage b[j][c][bins of the tile]: consecutive threads read consecutive bins
-      for (int e = threadIdx.x; e < nv * C * kTileBins; e += blockDim.x) {
-        const int img = e / kTileBins, bi = e - img * kTileBins;
+      // stage b[j][c][bins of the tile] (consecutive threads read consecutive bins; the bin
+      // of a thread is fixed, threadIdx.x % kTileBins) and the views' positions
+      {
+        const int bi = threadIdx.x & (kTileBins - 1);
         int qy, qx;
         bin_coords(min(tile * kTileBins + bi, Qs - 1), p.H, M, qy, qx);
-        bstage[e] = *p.b.at((long long)j0 * C + img, qy, qx, M);
+        for (int img = threadIdx.x / kTileBins; img < nv * C; img += blockDim.x / kTileBins)
+          bstage[img * kTileBins + bi] = *p.b.at((long long)j0 * C + img, qy, qx, M);
+        for (int j = threadIdx.x; j < nv; j += blockDim.x) ustage[j] = __ldg(reinterpret_cast<const float2*>(p.u) + j0 + j);
       }
       __syncthreads();
-      for (int jj = 0; jj < nv; ++jj) {
-        const int j = j0 + jj;
-        const float2 uj = __ldg(reinterpret_cast<const float2*>(p.u) + j);
-        float2 a = make_float2(0.f, 0.f);
-        if (lane < N) {
-          if (lat) {
-            // A_jr = P_r^a Q_r^b, conjugates for negative powers
-            const int ax = (int)uj.x, by = (int)uj.y;
-            float2 pa = make_float2(1.f, 0.f), qb = make_float2(1.f, 0.f);
-            if (ax != 0) pa = ptab[(abs(ax) - 1) * 32 + lane];
-            if (by != 0) qb = ptab[(kLatMax + abs(by) - 1) * 32 + lane];
-            if (ax < 0) pa.y = -pa.y;
-            if (by < 0) qb.y = -qb.y;
-            a = cmul(pa, qb);
-          } else {
-            const float f = phase_cycles(uj.x, uj.y, fq, dl);
-            sincospif(2.f * f, &a.y, &a.x);
+      if (mom) {
+        // moment form: per view one A_jr per lane (row r), w_jm = conj(A_j0) A_jm in lane m,
+        // W_0 += w, W_1 += theta_j w and the right-hand sides; no loop-carried dependence but
+        // the sums, so the unrolled views overlap their latencies
+#pragma unroll 4
+        for (int jj = 0; jj < nv; ++jj) {
+          const float2 uj = ustage[jj];
+          float2 a = make_float2(0.f, 0.f);
+          if (lane < N) {
+            if (lat) {
+              // A_jr = P_r^a Q_r^b, conjugates for negative powers
+              const int ax = (int)uj.x, by = (int)uj.y;
+              float2 pa = make_float2(1.f, 0.f), qb = make_float2(1.f, 0.f);
+              if (ax != 0) pa = ptab[(abs(ax) - 1) * 32 + lane];
+              if (by != 0) qb = ptab[(kLatMax + abs(by) - 1) * 32 + lane];
+              if (ax < 0) pa.y = -pa.y;
+              if (by < 0) qb.y = -qb.y;
+              a = cmul(pa, qb);
+            } else {
+              const float f = phase_cycles(uj.x, uj.y, fq, dl);
+              sincospif(2.f * f, &a.y, &a.x);
+            }
           }
-        }
-        if (mom) {
-          // w_jm = conj(A_j0) A_jm in lane m: W_0 += w, W_1 += theta_j w
           const float2 a0 = make_float2(__shfl_sync(0xffffffffu, a.x, 0), __shfl_sync(0xffffffffu, a.y, 0));
           const float2 w = cmulc(a0, a);
           const float th = fmaf(uj.x, wx, uj.y * wy);
@@ -139,7 +145,15 @@ __global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, 
               cfmac(y[c], a, bstage[(jj * C + c) * kTileBins + warp]);
             }
           }
-          continue;
+        }
+        continue;
+      }
+      for (int jj = 0; jj < nv; ++jj) {
+        const float2 uj = ustage[jj];
+        float2 a = make_float2(0.f, 0.f);
+        if (lane < N) {
+          const float f = phase_cycles(uj.x, uj.y, fq, dl);
+          sincospif(2.f * f, &a.y, &a.x);
         }
         if (lane < NMAX) myA[lane] = a;
         __syncwarp();
