@@ -88,10 +88,12 @@ struct FitWs {
   void* select;
   float2* spec_main;
   float2* spec_nyq;
+  float4* f32sums = nullptr;  // scratch of the FP32 solve's moment-form view sums (N <= 32)
+  int f32sums_tiles = 0;
   size_t bytes;
 };
 
-FitWs carve_fit(void* ws, int K, int C, int H, int W, bool with_spectra) {
+FitWs carve_fit(void* ws, int K, int C, int H, int W, int N, bool with_spectra, bool sums = true) {
   Carver cv(ws);
   FitWs f;
   f.counters = cv.take<int>(kHeaderInts);
@@ -103,6 +105,12 @@ FitWs carve_fit(void* ws, int K, int C, int H, int W, bool with_spectra) {
   f.err = cv.take<float>((size_t)H * (W / 2 + 1));
   f.xn2 = cv.take<float>((size_t)H * (W / 2 + 1));
   f.select = cv.take<char>(select_scratch_bytes());
+  if (sums && N <= 32) {
+    // the view sums of up to kF32SumsTiles tiles of 8 frequencies at a time
+    const int tiles = (int)std::min<long long>(((long long)H * (W / 2 + 1) + 7) / 8, kF32SumsTiles);
+    f.f32sums_tiles = tiles;
+    f.f32sums = cv.take<float4>((size_t)tiles * 8 * 32 * 3);  // float4 (W_0, W_1) + 4 float2 per lane
+  }
   if (with_spectra) {
     f.spec_main = cv.take<float2>((size_t)K * C * H * (W / 2));
     f.spec_nyq = cv.take<float2>((size_t)K * C * H);
@@ -153,6 +161,8 @@ int run_solve(SpecView b, int K, int C, int H, int W, const float* u, const floa
   p.counters = f.counters;
   p.exp_table = f.exp_table;
   p.mom = f.mom;
+  p.f32sums = f.f32sums;
+  p.f32sums_tiles = f.f32sums_tiles;
   cudaError_t e = cudaMemsetAsync(f.counters, 0, kHeaderInts * sizeof(int), st);
   if (e != cudaSuccess) return FDL_ECUDA;
   e = launch_exp_table(f.exp_table, st);
@@ -388,7 +398,7 @@ FDL_API int fdl_irfft2(const float* spectra, int nimg, int H, int W, float* imag
 // ------------------------------------------------------------------ fit
 FDL_API size_t fdl_fit_workspace_size(int K, int C, int H, int W, int N) {
   if (K < 1 || C < 1 || N < 1 || !shape_ok(H, W)) return 0;
-  return carve_fit(nullptr, K, C, H, W, true).bytes;
+  return carve_fit(nullptr, K, C, H, W, N, true).bytes;
 }
 
 FDL_API int fdl_fit(const float* views, int K, int C, int H, int W, const float* u, const float* d, int N,
@@ -398,7 +408,7 @@ FDL_API int fdl_fit(const float* views, int K, int C, int H, int W, const float*
   if (!views || !u || !d || !layers || !workspace) return FDL_EINVAL;
   if (workspace_bytes < fdl_fit_workspace_size(K, C, H, W, N)) return FDL_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  FitWs f = carve_fit(workspace, K, C, H, W, true);
+  FitWs f = carve_fit(workspace, K, C, H, W, N, true);
   const int nimg = K * C;
   if (!pow2_shape(H, W)) {
     // dense half spectra from spec_main (spec_main and spec_nyq are carved back to back)
@@ -420,7 +430,7 @@ FDL_API int fdl_fit(const float* views, int K, int C, int H, int W, const float*
 
 FDL_API size_t fdl_fit_spectra_workspace_size(int K, int C, int H, int W, int N) {
   if (K < 1 || C < 1 || N < 1 || !shape_ok(H, W)) return 0;
-  return carve_fit(nullptr, K, C, H, W, false).bytes;
+  return carve_fit(nullptr, K, C, H, W, N, false).bytes;
 }
 
 FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W, const float* u, const float* d, int N,
@@ -431,7 +441,7 @@ FDL_API int fdl_fit_spectra(const float* spectra, int K, int C, int H, int W, co
   if (!spectra || !u || !d || !layers || !workspace) return FDL_EINVAL;
   if (workspace_bytes < fdl_fit_spectra_workspace_size(K, C, H, W, N)) return FDL_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  FitWs f = carve_fit(workspace, K, C, H, W, false);
+  FitWs f = carve_fit(workspace, K, C, H, W, N, false);
   SpecView b = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
   return run_solve(b, K, C, H, W, u, d, N, opts, layers, f, st);
 }
@@ -615,7 +625,7 @@ FDL_API int fdl_calib_grad(const float* spectra, int K, int C, int H, int W, con
 // ------------------------------------------------------------------ general system
 FDL_API size_t fdl_fit_general_workspace_size(int K, int C, int H, int W, int N) {
   if (K < 1 || C < 1 || N < 1 || !shape_ok(H, W)) return 0;
-  return carve_fit(nullptr, K, C, H, W, false).bytes;
+  return carve_fit(nullptr, K, C, H, W, N, false, false).bytes;
 }
 
 FDL_API int fdl_fit_general(const float* spectra, int K, int C, int H, int W, int N, const fdl_system* sys,
@@ -628,7 +638,7 @@ FDL_API int fdl_fit_general(const float* spectra, int K, int C, int H, int W, in
   if ((sys->views || opts->reg == FDL_REG_VIEW2) && !sys->d) return FDL_EINVAL;
   if (workspace_bytes < fdl_fit_general_workspace_size(K, C, H, W, N)) return FDL_ENOMEM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  FitWs f = carve_fit(workspace, K, C, H, W, false);
+  FitWs f = carve_fit(workspace, K, C, H, W, N, false, false);
   SolveParams p{};
   p.b = spec_dense(const_cast<float2*>(reinterpret_cast<const float2*>(spectra)), H, W);
   p.x = reinterpret_cast<float2*>(layers);

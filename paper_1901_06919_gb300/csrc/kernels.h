@@ -66,8 +66,15 @@ struct SolveParams {
   // e_k = d_k - d_0 - k Delta as double-floats, written by the check kernel, which also
   // sets counters[8] to 1 when the moment form applies.
   float2* mom;
+  // Scratch of the FP32 solve's moment-form view sums (nullable: the solve kernel forms them
+  // itself), for f32sums_tiles tiles of 8 frequencies at a time: (W_0, W_1) float4
+  // [tiles x 8][32], then the right-hand sides float2 [tiles x 8][4][32].
+  float4* f32sums = nullptr;
+  int f32sums_tiles = 0;
 };
 constexpr int kMomSlots = 65;
+// the most tiles of 8 frequencies whose FP32 view sums one k_f32_sums launch writes
+constexpr int kF32SumsTiles = 16448;
 // FP32 solve of every stored bin; with estimate, also err / xn2 per bin (err = +inf
 // where the result is not trusted) and every bin counted in counters[0].
 cudaError_t launch_solve_f32(const SolveParams& p, bool estimate, cudaStream_t st);

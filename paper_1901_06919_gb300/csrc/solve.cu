@@ -25,6 +25,8 @@
 //    from which the caller picks the frequencies to re-solve more precisely.
 //  * k_solve_hp<T>: the same solve in double-float (T = Rdf) or native FP64
 //    (T = R64) for the listed frequencies (or for all of them).
+#include <algorithm>
+
 #include "hp_solve.cuh"
 
 namespace fdl {
@@ -35,9 +37,131 @@ constexpr int kTileBins = 8;    // bins per CTA tile = warps per CTA
 constexpr int kViewChunk = 128;  // views staged per pass (one pass for K <= 128)
 
 // ------------------------------------------------------------------ FP32
+// Per-lane lattice powers P_r^k, Q_r^k (k = 1..kLatMax) of this lane's row r at frequency fq;
+// only this lane reads them back.
+__device__ __forceinline__ void f32_lattice_powers(float2* ptab, int lane, int N, const Freq& fq, float dl) {
+  if (lane < N) {
+#pragma unroll 1
+    for (int k = 1; k <= kLatMax; ++k) {
+      float2 t;
+      sincospif(2.f * phase_cycles((float)k, 0.f, fq, dl), &t.y, &t.x);
+      ptab[(k - 1) * 32 + lane] = t;
+      sincospif(2.f * phase_cycles(0.f, (float)k, fq, dl), &t.y, &t.x);
+      ptab[(kLatMax + k - 1) * 32 + lane] = t;
+    }
+  }
+}
+
+// Stages views [j0, j0 + nv) of the tile's kTileBins frequencies: b[j][c][bin] (consecutive
+// threads read consecutive bins; a thread's bin is fixed, threadIdx.x % kTileBins) and u_j.
+// CTA-wide; the caller puts barriers around it.
+__device__ __forceinline__ void f32_stage(const SolveParams& p, int tile, int j0, int nv, int Qs, int M,
+                                          float2* bstage, float2* ustage) {
+  const int C = p.C;
+  const int bi = threadIdx.x & (kTileBins - 1);
+  int qy, qx;
+  bin_coords(min(tile * kTileBins + bi, Qs - 1), p.H, M, qy, qx);
+  for (int img = threadIdx.x / kTileBins; img < nv * C; img += blockDim.x / kTileBins)
+    bstage[img * kTileBins + bi] = *p.b.at((long long)j0 * C + img, qy, qx, M);
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) ustage[j] = __ldg(reinterpret_cast<const float2*>(p.u) + j0 + j);
+}
+
+// Moment form, per warp (frequency fq, lane m / row r): W_0(m) = sum_j w_jm, W_1(m) = sum_j
+// theta_j w_jm with w_jm = conj(A_j0) A_jm, and y_c(r) = sum_j conj(A_jr) b_jc over every view;
+// A from the lattice powers in ptab when lat, else from the phase.  CTA-wide (stages views).
+__device__ __forceinline__ void f32_mom_sums(const SolveParams& p, int tile, int Qs, int M, const Freq& fq, float dl,
+                                             bool lat, float2* bstage, float2* ustage, const float2* ptab,
+                                             float2& W0, float2& W1, float2 y[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int C = p.C, N = p.N, K = p.K;
+  const float wx = fq.wx, wy = fq.wy;
+  for (int j0 = 0; j0 < K; j0 += kViewChunk) {
+    const int nv = min(kViewChunk, K - j0);
+    __syncthreads();
+    f32_stage(p, tile, j0, nv, Qs, M, bstage, ustage);
+    __syncthreads();
+    // no loop-carried dependence but the sums, so the unrolled views overlap their latencies
+#pragma unroll 4
+    for (int jj = 0; jj < nv; ++jj) {
+      const float2 uj = ustage[jj];
+      float2 a = make_float2(0.f, 0.f);
+      if (lane < N) {
+        if (lat) {
+          // A_jr = P_r^a Q_r^b, conjugates for negative powers
+          const int ax = (int)uj.x, by = (int)uj.y;
+          float2 pa = make_float2(1.f, 0.f), qb = make_float2(1.f, 0.f);
+          if (ax != 0) pa = ptab[(abs(ax) - 1) * 32 + lane];
+          if (by != 0) qb = ptab[(kLatMax + abs(by) - 1) * 32 + lane];
+          if (ax < 0) pa.y = -pa.y;
+          if (by < 0) qb.y = -qb.y;
+          a = cmul(pa, qb);
+        } else {
+          const float f = phase_cycles(uj.x, uj.y, fq, dl);
+          sincospif(2.f * f, &a.y, &a.x);
+        }
+      }
+      const float2 a0 = make_float2(__shfl_sync(0xffffffffu, a.x, 0), __shfl_sync(0xffffffffu, a.y, 0));
+      const float2 w = cmulc(a0, a);
+      const float th = fmaf(uj.x, wx, uj.y * wy);
+      W0.x += w.x;
+      W0.y += w.y;
+      W1.x = fmaf(th, w.x, W1.x);
+      W1.y = fmaf(th, w.y, W1.y);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c < C) {
+          cfmac(y[c], a, bstage[(jj * C + c) * kTileBins + warp]);
+        }
+      }
+    }
+  }
+}
+
+// The moment-form sums of the FP32 solve for tiles [t0, t1) (kTileBins frequencies each), when
+// the moment form applies: wsum[i * 32 + lane] = (W_0, W_1) of lane m, ysum[(i * 4 + c) * 32 +
+// lane] = y_c of row r, i = (tile - t0) kTileBins + warp.  Few registers and 49 KB of shared
+// memory per CTA, so that four CTAs per SM hide the latencies of the view loop that the
+// register- and shared-memory-heavy solve kernel (two CTAs per SM) cannot; k_solve_f32 reads them.
+__global__ void __launch_bounds__(kTileBins * 32) k_f32_sums(SolveParams p, int t0, int t1, float4* __restrict__ wsum,
+                                                             float2* __restrict__ ysum) {
+  extern __shared__ float4 smem4[];
+  __shared__ float2 ustage[kViewChunk];
+  float2* bstage = reinterpret_cast<float2*>(smem4);             // [kViewChunk * 4][kTileBins]
+  float2* ptabs = bstage + kViewChunk * 4 * kTileBins;           // [kTileBins][2 kLatMax][32]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int M = p.W >> 1, N = p.N;
+  const bool mom = p.mom != nullptr && *((volatile int*)(p.counters + 8)) == 1;
+  if (!mom) return;
+  const bool lat = *((volatile int*)(p.counters + 10)) == 1;
+  float2* ptab = ptabs + warp * 2 * kLatMax * 32;
+  const int Qs = p.H * (M + 1);
+  const float dl = lane < N ? __ldg(p.d + lane) : 0.f;
+  for (int tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
+    const int q = min(tile * kTileBins + warp, Qs - 1);
+    int ky, kx;
+    bin_coords(q, p.H, M, ky, kx);
+    const Freq fq = bin_freq(ky, kx, p.H, p.W);
+    float2 y[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[c] = make_float2(0.f, 0.f);
+    float2 W0 = make_float2(0.f, 0.f), W1 = make_float2(0.f, 0.f);
+    if (lat) {
+      __syncwarp();  // the previous tile's reads of this lane's powers are done
+      f32_lattice_powers(ptab, lane, N, fq, dl);
+    }
+    f32_mom_sums(p, tile, Qs, M, fq, dl, lat, bstage, ustage, ptab, W0, W1, y);
+    const long long i = (long long)(tile - t0) * kTileBins + warp;
+    wsum[i * 32 + lane] = make_float4(W0.x, W0.y, W1.x, W1.y);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ysum[(i * 4 + c) * 32 + lane] = y[c];
+  }
+}
+
 template <int NMAX>
 // two CTAs per SM: the register allocation must stay within 128 per thread
-__global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, int estimate) {
+__global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, int estimate, int t0, int t1,
+                                                                  const float4* __restrict__ wsum,
+                                                                  const float2* __restrict__ ysum) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -63,7 +187,7 @@ __global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, 
   const float el = (mom && lane < N) ? p.mom[lane].x : 0.f;  // e_lane
   float2* ptab = myL;  // lattice powers [2 kLatMax][32] while the Gram matrix is built
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = t0 + blockIdx.x; tile < min(t1, ntiles); tile += gridDim.x) {
     // warps past the last bin of a partial tile solve the last bin again (every warp
     // takes part in the CTA's barriers) and write nothing
     const int q = min(tile * kTileBins + warp, Qs - 1);
@@ -80,97 +204,52 @@ __global__ void __launch_bounds__(kTileBins * 32, 2) k_solve_f32(SolveParams p, 
 #pragma unroll
     for (int c = 0; c < 4; ++c) y[c] = make_float2(0.f, 0.f);
     float2 W0 = make_float2(0.f, 0.f), W1 = make_float2(0.f, 0.f);  // moment sums, m = lane
-    if (lat) {
-      // P^k, Q^k of this lane's row; only this lane reads them back (the barrier orders
-      // the writes after the previous frequency's reads of the factor in the same words)
-      __syncwarp();
-      if (lane < N) {
-#pragma unroll 1
-        for (int k = 1; k <= kLatMax; ++k) {
-          float2 t;
-          sincospif(2.f * phase_cycles((float)k, 0.f, fq, dl), &t.y, &t.x);
-          ptab[(k - 1) * 32 + lane] = t;
-          sincospif(2.f * phase_cycles(0.f, (float)k, fq, dl), &t.y, &t.x);
-          ptab[(kLatMax + k - 1) * 32 + lane] = t;
-        }
+    if (mom && wsum != nullptr) {
+      // the sums of k_f32_sums
+      const long long i = (long long)(tile - t0) * kTileBins + warp;
+      const float4 w = wsum[i * 32 + lane];
+      W0 = make_float2(w.x, w.y);
+      W1 = make_float2(w.z, w.w);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y[c] = ysum[(i * 4 + c) * 32 + lane];
+    } else if (mom) {
+      if (lat) {
+        // P^k, Q^k of this lane's row in the words of its factor (the barrier orders the
+        // writes after the previous frequency's reads of the factor)
+        __syncwarp();
+        f32_lattice_powers(ptab, lane, N, fq, dl);
       }
-    }
-    for (int j0 = 0; j0 < K; j0 += kViewChunk) {
-      const int nv = min(kViewChunk, K - j0);
-      __syncthreads();
-      // stage b[j][c][bins of the tile] (consecutive threads read consecutive bins; the bin
-      // of a thread is fixed, threadIdx.x % kTileBins) and the views' positions
-      {
-        const int bi = threadIdx.x & (kTileBins - 1);
-        int qy, qx;
-        bin_coords(min(tile * kTileBins + bi, Qs - 1), p.H, M, qy, qx);
-        for (int img = threadIdx.x / kTileBins; img < nv * C; img += blockDim.x / kTileBins)
-          bstage[img * kTileBins + bi] = *p.b.at((long long)j0 * C + img, qy, qx, M);
-        for (int j = threadIdx.x; j < nv; j += blockDim.x) ustage[j] = __ldg(reinterpret_cast<const float2*>(p.u) + j0 + j);
-      }
-      __syncthreads();
-      if (mom) {
-        // moment form: per view one A_jr per lane (row r), w_jm = conj(A_j0) A_jm in lane m,
-        // W_0 += w, W_1 += theta_j w and the right-hand sides; no loop-carried dependence but
-        // the sums, so the unrolled views overlap their latencies
-#pragma unroll 4
+      f32_mom_sums(p, tile, Qs, M, fq, dl, lat, bstage, ustage, ptab, W0, W1, y);
+    } else {
+      for (int j0 = 0; j0 < K; j0 += kViewChunk) {
+        const int nv = min(kViewChunk, K - j0);
+        __syncthreads();
+        f32_stage(p, tile, j0, nv, Qs, M, bstage, ustage);
+        __syncthreads();
         for (int jj = 0; jj < nv; ++jj) {
           const float2 uj = ustage[jj];
           float2 a = make_float2(0.f, 0.f);
           if (lane < N) {
-            if (lat) {
-              // A_jr = P_r^a Q_r^b, conjugates for negative powers
-              const int ax = (int)uj.x, by = (int)uj.y;
-              float2 pa = make_float2(1.f, 0.f), qb = make_float2(1.f, 0.f);
-              if (ax != 0) pa = ptab[(abs(ax) - 1) * 32 + lane];
-              if (by != 0) qb = ptab[(kLatMax + abs(by) - 1) * 32 + lane];
-              if (ax < 0) pa.y = -pa.y;
-              if (by < 0) qb.y = -qb.y;
-              a = cmul(pa, qb);
-            } else {
-              const float f = phase_cycles(uj.x, uj.y, fq, dl);
-              sincospif(2.f * f, &a.y, &a.x);
-            }
+            const float f = phase_cycles(uj.x, uj.y, fq, dl);
+            sincospif(2.f * f, &a.y, &a.x);
           }
-          const float2 a0 = make_float2(__shfl_sync(0xffffffffu, a.x, 0), __shfl_sync(0xffffffffu, a.y, 0));
-          const float2 w = cmulc(a0, a);
-          const float th = fmaf(uj.x, wx, uj.y * wy);
-          W0.x += w.x;
-          W0.y += w.y;
-          W1.x = fmaf(th, w.x, W1.x);
-          W1.y = fmaf(th, w.y, W1.y);
+          if (lane < NMAX) myA[lane] = a;
+          __syncwarp();
+          const float4* A4 = reinterpret_cast<const float4*>(myA);
+#pragma unroll
+          for (int l2 = 0; l2 < NMAX / 2; ++l2) {
+            const float4 v = A4[l2];
+            cfmac(G[2 * l2], a, make_float2(v.x, v.y));
+            cfmac(G[2 * l2 + 1], a, make_float2(v.z, v.w));
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             if (c < C) {
               cfmac(y[c], a, bstage[(jj * C + c) * kTileBins + warp]);
             }
           }
+          __syncwarp();
         }
-        continue;
-      }
-      for (int jj = 0; jj < nv; ++jj) {
-        const float2 uj = ustage[jj];
-        float2 a = make_float2(0.f, 0.f);
-        if (lane < N) {
-          const float f = phase_cycles(uj.x, uj.y, fq, dl);
-          sincospif(2.f * f, &a.y, &a.x);
-        }
-        if (lane < NMAX) myA[lane] = a;
-        __syncwarp();
-        const float4* A4 = reinterpret_cast<const float4*>(myA);
-#pragma unroll
-        for (int l2 = 0; l2 < NMAX / 2; ++l2) {
-          const float4 v = A4[l2];
-          cfmac(G[2 * l2], a, make_float2(v.x, v.y));
-          cfmac(G[2 * l2 + 1], a, make_float2(v.z, v.w));
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (c < C) {
-            cfmac(y[c], a, bstage[(jj * C + c) * kTileBins + warp]);
-          }
-        }
-        __syncwarp();
       }
     }
 
@@ -459,11 +538,25 @@ template <int NMAX>
 cudaError_t launch_f32_n(const SolveParams& p, bool estimate, cudaStream_t st) {
   const size_t smem = (size_t)(kViewChunk * 4 * kTileBins + kTileBins * NMAX +
                                kTileBins * NMAX * (NMAX + 1)) * sizeof(float2);
+  const size_t smem_sums = (size_t)(kViewChunk * 4 * kTileBins + kTileBins * 2 * kLatMax * 32) * sizeof(float2);
   cudaError_t e = set_smem((const void*)k_solve_f32<NMAX>, smem);
+  if (e == cudaSuccess) e = set_smem((const void*)k_f32_sums, smem_sums);
   if (e != cudaSuccess) return e;
-  // one tile per CTA: short CTAs let higher-priority work interleave
+  // one tile per CTA: short CTAs let higher-priority work interleave; with p.f32sums the view
+  // sums of each chunk of tiles go first to their own kernel
   const int ntiles = (p.H * (p.W / 2 + 1) + kTileBins - 1) / kTileBins;
-  k_solve_f32<NMAX><<<ntiles, kTileBins * 32, smem, st>>>(p, estimate ? 1 : 0);
+  const int chunk = p.f32sums != nullptr ? p.f32sums_tiles : ntiles;
+  for (int t0 = 0; t0 < ntiles; t0 += chunk) {
+    const int t1 = std::min(ntiles, t0 + chunk);
+    float4* wsum = nullptr;
+    float2* ysum = nullptr;
+    if (p.f32sums != nullptr) {
+      wsum = p.f32sums;
+      ysum = reinterpret_cast<float2*>(p.f32sums + (size_t)p.f32sums_tiles * kTileBins * 32);
+      k_f32_sums<<<t1 - t0, kTileBins * 32, smem_sums, st>>>(p, t0, t1, wsum, ysum);
+    }
+    k_solve_f32<NMAX><<<t1 - t0, kTileBins * 32, smem, st>>>(p, estimate ? 1 : 0, t0, t1, wsum, ysum);
+  }
   return cudaGetLastError();
 }
 
