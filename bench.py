@@ -961,11 +961,12 @@ def main():
     legs = time_kernel_legs(path)
     p50, p99 = time_latency(path)
     # kernels per step (the ncu launch list of --case step): fit = 2 twiddle tables + rows +
-    # cols + exp table + moment check + FP32 solve + 3 selection + 2 double-float solves (one
-    # exits at once) + 3 selection + FP64 solve + status = 16; fdl_render = requests + render +
+    # cols + exp table + moment check + FP32 view sums + FP32 solve + 3 selection + 2
+    # double-float solves (one exits at once) + 3 selection + FP64 solve + status = 17;
+    # fdl_render = requests + render +
     # column and row passes = 4; fdl_refocus = plan + 4 launches of the mixed path (return at
     # once) + render + column and row passes = 8
-    launches = 16 + 4 + 8
+    launches = 17 + 4 + 8
 
     fit_ms = stages["fit_ms"]
     render_ms = stages["render81_ms"] + stages["refocus32_ms"]
@@ -1014,8 +1015,8 @@ def main():
         sat = line["serving"]["saturation_render_only"]
         line["roofline_stages"].append({"stage": "serving render at saturation (2,000 mixed-size requests at once, "
                                                  "batches of up to 32)",
-                                        "kernel": "k_render_gate + k_render_cols (x2) + k_irfft_rows_req "
-                                                  "(+ the tiled passes, gated off)", "bound": "hbm",
+                                        "kernel": "k_render_plan + k_render_grp + k_cols_req (x2) + "
+                                                  "k_irfft_rows_req (+ the tiled passes, gated off)", "bound": "hbm",
                                         "achieved": sat["alg_gbs_device"], "peak": hbm, "unit": "GB/s",
                                         "frac": sat["alg_gbs_device"] / hbm, "algorithmic_bytes": sat["alg_bytes"],
                                         "traffic": None, "peak_source": src, "ms": sat["busy_ms"],
@@ -1059,9 +1060,9 @@ FP32_METHOD_FLOPS_PER_FREQUENCY = 145_000
 # 2,664 per frequency.
 DF_DRAM_BYTES_PER_FREQUENCY = (270.752e6 + 79.548672e6) / 131_584
 DF_WARP_INSTRUCTIONS_PER_FREQUENCY = 9_554_976_035 / 131_584
-# The FP32 solve (k_solve_f32<32>, the pass with estimates, bench.py --case step): DRAM bytes per
-# launch over all 131,584 frequencies.
-F32_DRAM_BYTES = 257.351168e6 + 73.79072e6
+# The FP32 solve (k_f32_sums + k_solve_f32<32>, the pass with estimates, bench.py --case step):
+# DRAM bytes per pass over all 131,584 frequencies (the view sums go through workspace scratch).
+F32_DRAM_BYTES = (256.081408e6 + 163.084544e6) + (203.742464e6 + 64.532992e6)
 
 
 # ------------------------------------------------------------------ bounded cases for profilers
@@ -1195,7 +1196,8 @@ def stage_rooflines(legs, clk):
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     f32 = FP32_METHOD_FLOPS_PER_FREQUENCY * q_half() / (legs["solve_f32_all_ms"] / 1e3) / 1e12
     tiled = "k_render + k_fft_cols<inverse> + k_irfft_rows"
-    return [{"stage": "FP32 solve of every frequency (no estimate)", "kernel": "k_solve_f32<32>", "bound": "alu",
+    return [{"stage": "FP32 solve of every frequency (no estimate)", "kernel": "k_f32_sums + k_solve_f32<32>",
+             "bound": "alu",
              "achieved": f32, "peak": peak, "unit": "TFLOP/s", "frac": f32 / peak,
              "ms": legs["solve_f32_all_ms"], "traffic": F32_DRAM_BYTES,
              "algorithmic_bytes": (K + N) * C * 8 * q_half(),
@@ -1211,7 +1213,7 @@ def stage_rooflines(legs, clk):
 # captured), all from bench.py --case render81: the forward DFT's two passes, and the tiled
 # render of the 81 views (k_render, the inverse column pass, the row pass).
 DFT_DRAM_BYTES = (254.834944e6 + 209.893632e6) + (254.8416e6 + 201.214976e6)
-RENDER81_DRAM_BYTES = (99.3e6 + 201.2e6) + (255.831552e6 + 193.479168e6) + (254.873088e6 + 212.408064e6)
+RENDER81_DRAM_BYTES = (99.271936e6 + 198.1056e6) + (255.84896e6 + 190.7136e6) + (254.875136e6 + 206.172672e6)
 
 
 if __name__ == "__main__":
