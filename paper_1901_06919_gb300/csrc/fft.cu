@@ -152,8 +152,11 @@ __global__ void __launch_bounds__(512) k_fft_cols(SpecView in, SpecView out, int
   }
 }
 
+// columns per CTA of the inverse column pass: 4096 / H (8 at H = 512, 64-byte row segments;
+// measured on 81 views of 512^2 RGB: 16 columns 0.94 ms, 8 columns 0.90 ms, 4 columns 0.91 ms
+// for the whole render), within [4, 16]
 int strip_width(int H, int W) {
-  int sw = 8192 / H;
+  int sw = 4096 / H;
   if (sw > 16) sw = 16;
   if (sw < 4) sw = 4;
   if (sw > W / 2) sw = W / 2;
