@@ -1140,7 +1140,19 @@ def case_step():
     print(json.dumps({"case": "step", "tiers": path.F.FitWorkspace.tier_counts(path.ws_fit)}))
 
 
-CASES = {"df512": case_df512, "render81": case_render81, "mixed_batch": case_mixed_batch, "step": case_step}
+def case_refocus32():
+    """The 32 disc-aperture refocused images of the benchmark step, twice, after the fit."""
+    torch, dev = _case_device()
+    views, u, d, s_list = workload_inputs()
+    path = FdlPath(dev, views, u, d, s_list)
+    for _ in range(2):
+        path.refocus()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "refocus32"}))
+
+
+CASES = {"df512": case_df512, "render81": case_render81, "mixed_batch": case_mixed_batch, "refocus32": case_refocus32,
+         "step": case_step}
 
 
 def measured_hbm():
@@ -1206,7 +1218,8 @@ def stage_rooflines(legs, clk):
                          K * img + K * C * q_half() * 8, legs["rfft2_ms"], DFT_DRAM_BYTES),
             roofline_hbm("render of the 81 input views", tiled, layers + K * img, legs["render81_ms"],
                          RENDER81_DRAM_BYTES),
-            roofline_hbm("32 refocused images (disc)", tiled, layers + N_REFOCUS * img, legs["refocus32_ms"], None)]
+            roofline_hbm("32 refocused images (disc)", tiled, layers + N_REFOCUS * img, legs["refocus32_ms"],
+                         REFOCUS32_DRAM_BYTES)]
 
 
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels (None: not
@@ -1214,6 +1227,8 @@ def stage_rooflines(legs, clk):
 # render of the 81 views (k_render, the inverse column pass, the row pass).
 DFT_DRAM_BYTES = (254.834944e6 + 209.893632e6) + (254.8416e6 + 201.214976e6)
 RENDER81_DRAM_BYTES = (99.271936e6 + 198.1056e6) + (255.84896e6 + 190.7136e6) + (254.875136e6 + 206.172672e6)
+# the 32 refocused images (the same three kernels, bench.py --case refocus32)
+REFOCUS32_DRAM_BYTES = (98.184704e6 + 55.065088e6) + (101.079296e6 + 42.461952e6) + (100.725248e6 + 52.825088e6)
 
 
 if __name__ == "__main__":
