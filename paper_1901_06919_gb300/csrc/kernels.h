@@ -11,6 +11,8 @@ namespace fdl {
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
 // current device; the attribute is set once per (kernel, device, size).
 cudaError_t set_smem(const void* kernel, size_t bytes);
+// SM count of the current device (queried once per process)
+int num_sms();
 
 // ---- FFT (fft.cu) ----------------------------------------------------------
 // Inverse column pass: half spectra `in` (any layout) -> split layout `out`

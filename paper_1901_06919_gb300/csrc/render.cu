@@ -857,12 +857,8 @@ cudaError_t launch_render_mixed(const fdl_request* req, int B, const int* count,
   const long long se = (long long)render_mixed_slot_elems(C, H, W);
   const int M = W / 2;
   // render: a persistent grid over the plan's work items (at most B tiles of the largest size)
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
   const long long items = (long long)B * (((long long)H * (M + 1) + 31) / 32);
-  const int grid_r = (int)std::min<long long>(items, (long long)(sms > 0 ? sms : 148) * 12);
+  const int grid_r = (int)std::min<long long>(items, (long long)num_sms() * 12);
   const size_t smem_r = (size_t)Nmax * C * 32 * sizeof(float2);
   // inverse column pass: a request within (C, H, W) has at most as many strips and row blocks
   // as one of that size
@@ -871,7 +867,7 @@ cudaError_t launch_render_mixed(const fdl_request* req, int B, const int* count,
   const size_t smem_main = (size_t)(H + (size_t)C * (H > kRcFreqs ? H : kRcFreqs)) * sizeof(float2);
   const size_t smem_first = (size_t)(H + 2 * (size_t)C * H) * sizeof(float2);
   const size_t smem_rows = (size_t)(M + kRcFreqs) * sizeof(float2);
-  e = set_smem((const void*)k_render_grp<4>, smem_r);
+  cudaError_t e = set_smem((const void*)k_render_grp<4>, smem_r);
   if (e == cudaSuccess) e = set_smem((const void*)k_cols_req<false>, smem_main);
   if (e == cudaSuccess) e = set_smem((const void*)k_cols_req<true>, smem_first);
   if (e == cudaSuccess) e = set_smem((const void*)k_irfft_rows_req, smem_rows);

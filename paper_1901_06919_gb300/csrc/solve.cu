@@ -31,6 +31,18 @@
 
 namespace fdl {
 
+// SM count of the current device (queried once)
+static int g_num_sms = 0;
+int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
 namespace {
 
 constexpr int kTileBins = 8;    // bins per CTA tile = warps per CTA
@@ -523,16 +535,6 @@ __global__ void k_exp_table(float4* tab) {
   }
 }
 
-int g_num_sms = 0;
-int num_sms() {
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
-  }
-  return g_num_sms;
-}
 
 template <int NMAX>
 cudaError_t launch_f32_n(const SolveParams& p, bool estimate, cudaStream_t st) {
@@ -569,9 +571,12 @@ cudaError_t launch_hp_t(const SolveParams& p, bool all_bins, int list, cudaStrea
   const size_t smem = per_warp * warps;
   cudaError_t e = set_smem((const void*)k_solve_hp<T>, smem);
   if (e != cudaSuccess) return e;
-  // one frequency per warp for the largest possible list (CTAs past the list length exit)
+  // every frequency: one per warp; a list (its length known on the device only, usually
+  // short or empty): at most 8 CTAs per SM that stride over it, so that an empty list costs a
+  // few microseconds instead of one CTA launch per possible entry
   const int bins = p.H * (p.W / 2 + 1);
-  const int grid = (bins + warps - 1) / warps;
+  int grid = (bins + warps - 1) / warps;
+  if (!all_bins) grid = std::min(grid, 8 * num_sms());
   k_solve_hp<T><<<grid, warps * 32, smem, st>>>(p, all_bins ? 1 : 0, warps, list);
   return cudaGetLastError();
 }

@@ -33,6 +33,8 @@
 // x ~ 5e-6 for |u| <= 4); k_mom_check decides that on the device and exactly one of the
 // two kernels does the work.  Precision: W_0 in double-float as K + sum (w - 1), W_1 in
 // double-float (its term is ~2x of G), W_2, W_3 in FP32 (terms below 2x^2 and 2x^3 of G).
+#include <algorithm>
+
 #include "hp_solve.cuh"
 
 namespace fdl {
@@ -985,9 +987,13 @@ cudaError_t launch_df_v(const SolveParams& p, bool all_bins, cudaStream_t st) {
   cudaError_t e = set_smem((const void*)k_solve_df<NMAX, S, MOM>, smem);
   if (e != cudaSuccess) return e;
   // one frequency per warp for the largest possible list: short CTAs let
-  // higher-priority streams interleave (CTAs past the list length exit at once)
+  // higher-priority streams interleave (CTAs past the list length exit at once).  The general
+  // kernel launched beside the moment-form one (one of them returns at once, decided on the
+  // device) strides with at most 8 CTAs per SM, so that returning costs a few microseconds.
   const int bins = p.H * (p.W / 2 + 1);
-  k_solve_df<NMAX, S, MOM><<<(bins + kDfWarps - 1) / kDfWarps, kDfWarps * 32, smem, st>>>(p, all_bins ? 1 : 0);
+  int grid = (bins + kDfWarps - 1) / kDfWarps;
+  if (!MOM && p.mom != nullptr) grid = std::min(grid, 8 * num_sms());
+  k_solve_df<NMAX, S, MOM><<<grid, kDfWarps * 32, smem, st>>>(p, all_bins ? 1 : 0);
   return cudaGetLastError();
 }
 
