@@ -175,34 +175,37 @@ def time_device_steps(path, steps, warmup):
 def time_e2e(path, views_host, steps, warmup):
     """Views from pinned host memory -> fit -> 81 + 32 images back to pinned host memory, each
     step one call of the C ABI's fdl_fit_render_host (copies, fit and render enqueued by the
-    library) on one of two streams, so that the copies of one step overlap the computation of
-    the next.  Device span from the first copy-in to the last copy-out, CUDA events."""
+    library) on one of three streams, so that the copies of one step overlap the computation of
+    its neighbours.  Device span from the first copy-in to the last copy-out, CUDA events."""
     torch = path.torch
     from paper_1901_06919_gb300.pipeline import FitRenderPipeline
 
     refocus = [((0.0, 0.0), float(s), "disc", 1.0) for s in path.s_list]
     pipe = FitRenderPipeline(len(path.u), C, H, W, path.u, path.d, LAM, EPS, u0=path.u0, refocus=refocus,
                              device=path.dev)
+    ns = len(pipe.slots)
     out_host = [torch.empty((len(path.u0) + len(refocus), C, H, W), dtype=torch.float32).pin_memory()
-                for _ in range(2)]
+                for _ in range(ns)]
     for i in range(warmup):
-        pipe.submit(views_host, out_host[i % 2])
+        pipe.submit(views_host, out_host[i % ns])
     pipe.wait()
     torch.cuda.synchronize()
-    s0, s1 = pipe.slots[0]["stream"], pipe.slots[1]["stream"]
+    streams = [sl["stream"] for sl in pipe.slots]
     a = torch.cuda.Event(enable_timing=True)
-    a.record(s0)
-    s1.wait_event(a)
+    a.record(streams[0])
+    for s in streams[1:]:
+        s.wait_event(a)
     n0 = pipe.n
     for i in range(steps):
-        pipe.submit(views_host, out_host[(n0 + i) % 2])
-    b0 = torch.cuda.Event(enable_timing=True)
-    b1 = torch.cuda.Event(enable_timing=True)
-    b0.record(s0)
-    b1.record(s1)
+        pipe.submit(views_host, out_host[(n0 + i) % ns])
+    ends = []
+    for s in streams:
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(s)
+        ends.append(ev)
     pipe.wait()
     torch.cuda.synchronize()
-    ms = max(a.elapsed_time(b0), a.elapsed_time(b1)) / steps
+    ms = max(a.elapsed_time(ev) for ev in ends) / steps
     return ms, views_host.numel() * 4, out_host[0].numel() * 4
 
 
@@ -988,7 +991,7 @@ def main():
         "e2e": {"value": world * q_half() / (e2e_ms / 1e3) / 1e6, "unit": "Mfreq/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "fdl_fit_render_host (C ABI: views from pinned host memory, fit, 113 renders, images back to "
-                       "pinned host memory), alternating two streams and two device slots"},
+                       "pinned host memory), rotating over three streams and three device slots"},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
         "roofline": rl,

