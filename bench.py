@@ -218,17 +218,21 @@ def time_kernel_legs(path, reps=10):
     ws_s = None
 
     def timed(fn, n=reps):
+        # median of per-call device times (events around each call on the current stream):
+        # one call disturbed by other work on a shared GPU does not move it
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
+        evs = []
         for _ in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
             fn()
-        b.record()
+            b.record()
+            evs.append((a, b))
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / n
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
 
     out["rfft2_ms"] = timed(lambda: F.rfft2(path.views))
     _, ws_s = F.fit_spectra(spectra, path.u, path.d, LAM, EPS, out=path.layers)
@@ -237,7 +241,7 @@ def time_kernel_legs(path, reps=10):
     out["solve_f32_all_ms"] = timed(lambda: F.fit_spectra(spectra, path.u, path.d, LAM, EPS, precision="f32",
                                                           out=path.layers, ws=ws_s))
     out["solve_df_all_ms"] = timed(lambda: F.fit_spectra(spectra, path.u, path.d, LAM, EPS, precision="df",
-                                                         out=path.layers, ws=ws_s), n=3)
+                                                         out=path.layers, ws=ws_s), n=5)
     out["solve_df_all_tiers"] = ws_s.tier_counts()
     # the library's own native FP64 solve at every frequency (a second FP64 reference)
     out["solve_f64_all_ms"] = timed(lambda: F.fit_spectra(spectra, path.u, path.d, LAM, EPS, precision="f64",
