@@ -1232,7 +1232,7 @@ def stage_rooflines(legs, clk):
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels (None: not
 # captured), all from bench.py --case render81: the forward DFT's two passes, and the tiled
 # render of the 81 views (k_render, the inverse column pass, the row pass).
-DFT_DRAM_BYTES = (254.834944e6 + 209.893632e6) + (254.8416e6 + 201.214976e6)
+DFT_DRAM_BYTES = (254.848e6 + 209.98144e6) + (254.979328e6 + 197.8944e6)
 RENDER81_DRAM_BYTES = (99.271936e6 + 198.1056e6) + (255.84896e6 + 190.7136e6) + (254.875136e6 + 206.172672e6)
 # the 32 refocused images (the same three kernels, bench.py --case refocus32)
 REFOCUS32_DRAM_BYTES = (98.184704e6 + 55.065088e6) + (101.079296e6 + 42.461952e6) + (100.725248e6 + 52.825088e6)
