@@ -172,11 +172,12 @@ def time_device_steps(path, steps, warmup):
     return total, {"fit_ms": fit_ms, "render81_ms": render_ms, "refocus32_ms": refocus_ms}
 
 
-def time_e2e(path, views_host, steps, warmup):
+def time_e2e(path, views_host, steps, warmup, rounds=3):
     """Views from pinned host memory -> fit -> 81 + 32 images back to pinned host memory, each
     step one call of the C ABI's fdl_fit_render_host (copies, fit and render enqueued by the
     library) on one of three streams, so that the copies of one step overlap the computation of
-    its neighbours.  Device span from the first copy-in to the last copy-out, CUDA events."""
+    its neighbours.  Device span from the first copy-in to the last copy-out, CUDA events, per
+    step; the median of `rounds` such spans of `steps` steps."""
     torch = path.torch
     from paper_1901_06919_gb300.pipeline import FitRenderPipeline
 
@@ -191,22 +192,26 @@ def time_e2e(path, views_host, steps, warmup):
     pipe.wait()
     torch.cuda.synchronize()
     streams = [sl["stream"] for sl in pipe.slots]
-    a = torch.cuda.Event(enable_timing=True)
-    a.record(streams[0])
-    for s in streams[1:]:
-        s.wait_event(a)
-    n0 = pipe.n
-    for i in range(steps):
-        pipe.submit(views_host, out_host[(n0 + i) % ns])
-    ends = []
-    for s in streams:
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(s)
-        ends.append(ev)
-    pipe.wait()
-    torch.cuda.synchronize()
-    ms = max(a.elapsed_time(ev) for ev in ends) / steps
-    return ms, views_host.numel() * 4, out_host[0].numel() * 4
+    spans = []
+    for _ in range(rounds):
+        a = torch.cuda.Event(enable_timing=True)
+        a.record(streams[0])
+        for s in streams[1:]:
+            s.wait_event(a)
+        n0 = pipe.n
+        for i in range(steps):
+            pipe.submit(views_host, out_host[(n0 + i) % ns])
+        ends = []
+        for s in streams:
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+            ends.append(ev)
+        pipe.wait()
+        torch.cuda.synchronize()
+        spans.append(max(a.elapsed_time(ev) for ev in ends) / steps)
+    # the median of the rounds: the copies share the host's memory and NVLink-C2C with whatever
+    # else the machine runs, and one disturbed round does not move it
+    return float(np.median(spans)), views_host.numel() * 4, out_host[0].numel() * 4
 
 
 def time_kernel_legs(path, reps=10):
