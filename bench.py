@@ -1163,8 +1163,18 @@ def case_refocus32():
     print(json.dumps({"case": "refocus32"}))
 
 
+def case_latency():
+    """Sixteen single-image requests (views and discs), one at a time, after the fit: the
+    latency leg's launches."""
+    torch, dev = _case_device()
+    views, u, d, s_list = workload_inputs()
+    path = FdlPath(dev, views, u, d, s_list)
+    p50, p99 = time_latency(path, n=16)
+    print(json.dumps({"case": "latency", "p50_ms": p50, "p99_ms": p99}))
+
+
 CASES = {"df512": case_df512, "render81": case_render81, "mixed_batch": case_mixed_batch, "refocus32": case_refocus32,
-         "step": case_step}
+         "latency": case_latency, "step": case_step}
 
 
 def measured_hbm():

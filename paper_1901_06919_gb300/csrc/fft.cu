@@ -154,11 +154,13 @@ __global__ void __launch_bounds__(512) k_fft_cols(SpecView in, SpecView out, int
 
 // columns per CTA of the inverse column pass: 4096 / H (8 at H = 512, 64-byte row segments;
 // measured on 81 views of 512^2 RGB: 16 columns 0.94 ms, 8 columns 0.90 ms, 4 columns 0.91 ms
-// for the whole render), within [4, 16]
-int strip_width(int H, int W) {
+// for the whole render), within [4, 16]; halved (not below 4) while the launch of nimg images
+// would leave SMs without a strip (a single image: its latency is the whole point)
+int strip_width(int H, int W, long long nimg) {
   int sw = 4096 / H;
   if (sw > 16) sw = 16;
   if (sw < 4) sw = 4;
+  while (sw > 4 && (long long)(W / 2 / sw) * nimg < num_sms()) sw >>= 1;
   if (sw > W / 2) sw = W / 2;
   return sw;
 }
@@ -166,7 +168,7 @@ int strip_width(int H, int W) {
 template <bool INV>
 cudaError_t launch_cols(SpecView in, SpecView out, int nimg, int H, int W, const int* count, int C,
                         cudaStream_t st, const int* gate = nullptr) {
-  const int SW = strip_width(H, W);
+  const int SW = strip_width(H, W, nimg);
   const int T = 512;
   const int bpt = (SW * H / 4 + T - 1) / T;  // butterflies per thread per pass
   const size_t smem = (size_t)(H + SW * H) * sizeof(float2);
@@ -216,7 +218,9 @@ cudaError_t launch_irfft_rows(const float2* in, float* out, long long nrows, int
   // where that would exceed kMaxRowsPerCta rows
   const int M = W / 2;
   const int T = (M / 4 > 256) ? M / 4 : 256;
-  const int mb = M >= 16 ? 2 : 1;
+  // one butterfly per thread and pass where two would leave SMs without a CTA (a single image)
+  int mb = M >= 16 ? 2 : 1;
+  if (mb == 2 && (nrows + 2 * T / (M / 4) - 1) / (2 * T / (M / 4)) < 2 * num_sms()) mb = 1;
   const int R = mb * T / (M / 4);
   const size_t smem = (size_t)(M + R * M) * sizeof(float2);
   const long long grid = (nrows + R - 1) / R;

@@ -116,18 +116,41 @@ __device__ __forceinline__ float phase_from_theta(df theta, float d) {
 constexpr int kRenderWarps = 8;
 constexpr int kTileMaxLC = 256;  // N * C of an FDL staged in shared memory
 
+// Staging of a tile of layer values, tile[e] = x0[(e / 32) * plane + off] for e < nlc * 32 (this
+// thread's frequency at element offset off; zeros where !valid), by asynchronous global-to-shared
+// copies of 8 bytes: every thread's copies are in flight at once and hold no registers.  The
+// block is a multiple of 32 threads, so e % 32 is the lane.  Completion: cp_async_wait<n>
+// (all but the n most recently committed groups of this thread), then a barrier.
+__device__ __forceinline__ void stage_async(float2* tile, const float2* __restrict__ x0, int nlc, long long plane,
+                                            long long off, bool valid) {
+  const int n = nlc * 32;
+  const unsigned base = (unsigned)__cvta_generic_to_shared(tile);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const float2* src = valid ? x0 + (long long)(e >> 5) * plane + off : x0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(base + 8u * (unsigned)e), "l"(src),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
 // sum over layers k = k0, k0 + kstep, ... < r.N of the Eq. BsFourier terms of request r at
 // this lane's frequency; layer values from the shared tile (TILE) or from global memory;
 // SHIFTS: the request's per-layer shifts P_k in shb (the relaxed model), else u0 d_k.
 // AP: 0 no aperture factor (pinhole, or a disc of radius 0), 1 disc, 2 drawn (table),
-// 3 square or points.
-template <int CC, bool TILE, bool SHIFTS, int AP>
+// 3 square or points.  UNR: layers unrolled (their global loads in flight together).
+template <int CC, bool TILE, bool SHIFTS, int AP, int UNR>
 __device__ __forceinline__ void render_terms_t(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                                float wx, float wabs, long long plane, long long off, bool valid,
                                                const float2* tile, const float* dsh, int lane, float2 acc[4],
                                                const float2* __restrict__ shb, const Freq& fq) {
   const float2* x = reinterpret_cast<const float2*>(r.layers);
   const float zscale = 6.283185307f * r.radius * wabs;  // 2 pi r |w|
+#pragma unroll(UNR)
   for (int k = k0; k < r.N; k += kstep) {
     const float dk = TILE ? dsh[k] : __ldg(r.d + k);
     float ph;
@@ -160,7 +183,7 @@ __device__ __forceinline__ void render_terms_t(const fdl_request& r, int k0, int
   }
 }
 
-template <int CC, bool TILE, bool SHIFTS>
+template <int CC, bool TILE, bool SHIFTS, int UNR>
 __device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                                 float wx, float wabs, long long plane, long long off, bool valid,
                                                 const float2* tile, const float* dsh, int lane, float2 acc[4],
@@ -170,7 +193,7 @@ __device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, in
                  : r.aperture == FDL_AP_TABLE                                                 ? 2
                                                                                               : 3;
 #define FDL_TERMS(A) \
-  render_terms_t<CC, TILE, SHIFTS, A>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq)
+  render_terms_t<CC, TILE, SHIFTS, A, UNR>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, shb, fq)
   if (ap == 0) FDL_TERMS(0);
   else if (ap == 1) FDL_TERMS(1);
   else if (ap == 2) FDL_TERMS(2);
@@ -182,13 +205,14 @@ __device__ __forceinline__ void render_terms_ap(const fdl_request& r, int k0, in
 // and the aperture kind (all uniform over the request).  The phase factor is evaluated
 // directly at every layer here: a recurrence across layers measured slower in this kernel
 // (a dependent chain per warp and request, and its set-up for the few layers each warp
-// takes when the layers of one request are split across warps).
-template <int CC>
+// takes when the layers of one request are split across warps).  UNR applies to the layers
+// read from global memory.
+template <int CC, int UNR = 1>
 __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int kstep, int C, df theta, float wy,
                                              float wx, float wabs, long long plane, long long off, bool valid,
                                              const float2* tile, const float* dsh, int lane, float2 acc[4],
                                              const float2* __restrict__ shb, const Freq& fq) {
-#define FDL_AP(T, S) render_terms_ap<CC, T, S>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, \
+#define FDL_AP(T, S) render_terms_ap<CC, T, S, T ? 1 : UNR>(r, k0, kstep, C, theta, wy, wx, wabs, plane, off, valid, tile, dsh, lane, acc, \
                                           shb, fq)
   if (tile != nullptr) {
     if (shb != nullptr) FDL_AP(true, true);
@@ -202,15 +226,16 @@ __device__ __forceinline__ void render_terms(const fdl_request& r, int k0, int k
 
 // Two requests of one FDL, pinhole (AP 0) or disc (AP 1), no shift model: one pass over the
 // layers loads each layer value once for both (from the shared tile when TILE, else from
-// global memory at plane stride) and keeps two independent chains of phase, aperture and sums
-// in flight.
-template <int CC, int AP, bool TILE = true>
+// global memory at plane stride, UNR layers unrolled) and keeps two independent chains of
+// phase, aperture and sums in flight.
+template <int CC, int AP, bool TILE = true, int UNR = 1>
 __device__ __forceinline__ void render_pair(const fdl_request& r1, const fdl_request& r2, int C, df th1, df th2,
                                             float wabs, bool valid, const float2* tile, const float* dsh, int lane,
                                             float2 acc1[4], float2 acc2[4], long long plane = 0,
                                             long long off = 0) {
   const float z1 = 6.283185307f * r1.radius * wabs, z2 = 6.283185307f * r2.radius * wabs;
   const float2* x = reinterpret_cast<const float2*>(r1.layers);
+#pragma unroll(UNR)
   for (int k = 0; k < r1.N; ++k) {
     const float dk = TILE ? dsh[k] : __ldg(r1.d + k);
     float2 c1, c2;
@@ -313,12 +338,10 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
   __syncthreads();
   const bool shared = uniform && N0 * C <= tile_lc && N0 <= 64;
   if (shared) {
-    const float2* x0 = reinterpret_cast<const float2*>(L0);
-    // element e = (layer, channel) e / 32 at this thread's own frequency (e % 32 = lane: the
-    // block is a multiple of 32 threads)
-    for (int e = threadIdx.x; e < N0 * C * 32; e += blockDim.x)
-      tile[e] = valid ? __ldg(x0 + (long long)(e >> 5) * plane + off) : make_float2(0.f, 0.f);
+    stage_async(tile, reinterpret_cast<const float2*>(L0), N0 * C, plane, off, valid);
+    cp_async_commit();
     for (int k = threadIdx.x; k < N0; k += blockDim.x) dsh[k] = __ldg(req[0].d + k);
+    cp_async_wait<0>();
     __syncthreads();
   }
   for (int b = warp; b < Bact; b += kRenderWarps) {
@@ -366,6 +389,83 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request*
       for (int c = 0; c < 4; ++c)
         if (c < C) *out.at((long long)b * C + c, ky, kx, M) = acc[c];
     }
+  }
+}
+
+// two requests read one FDL (the same layer values, disparities and sizes)
+__device__ __forceinline__ bool same_fdl(const fdl_request& a, const fdl_request& b) {
+  return a.layers == b.layers && a.d == b.d && a.N == b.N && a.H == b.H && a.W == b.W && a.C == b.C;
+}
+
+// Fewer than 8 requests (single renders, small batches): each warp takes its own 32 consecutive
+// stored bins (lane = bin) and renders every request there, reading the layer values from
+// global memory (a layer value is used by at most B < 8 requests: staging it in shared memory
+// costs more instructions than it saves), two requests at a time where render_pair applies.
+// Setting up a frequency (its coordinates, w as a double-float, u0 . w) is done once per
+// request, not once per warp of a layer split.
+constexpr int kFewWarps = 4;  // CTAs of 128 threads: a single 512^2 render (1028 CTAs) fits one wave
+template <int CC>
+__global__ void __launch_bounds__(kFewWarps * 32) k_render_few(const fdl_request* __restrict__ req, int B,
+                                                                  const int* __restrict__ count, int C, int H, int W,
+                                                                  int nmax, SpecView out,
+                                                                  const float* __restrict__ shifts,
+                                                                  int* __restrict__ status,
+                                                                  const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int M = W >> 1;
+  const int Qs = H * (M + 1);
+  const long long plane = (long long)H * (M + 1);
+  const int Bact = count ? min(*count, B) : B;
+  const int q = (blockIdx.x * kFewWarps + warp) * 32 + lane;
+  if (Bact <= 0 || q - lane >= Qs) return;  // this warp's 32 bins lie past the image
+  const bool valid = q < Qs;
+  int ky, kx;
+  bin_coords(valid ? q : 0, H, M, ky, kx);
+  const Freq fq = bin_freq(ky, kx, H, W);
+  const float wabs = sqrtf(fq.wx * fq.wx + fq.wy * fq.wy);
+  const long long off = (long long)ky * (M + 1) + kx;
+  auto theta_of = [&](const fdl_request& r) {
+    return df_add_f(df_add(two_prod(r.u0x, fq.wx), two_prod(r.u0y, fq.wy)), fmaf(r.u0x, fq.wx_lo, r.u0y * fq.wy_lo));
+  };
+  auto put = [&](int b, const float2* a) {
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < C) *out.at((long long)b * C + c, ky, kx, M) = a[c];
+    }
+  };
+  for (int b = 0; b < Bact; ++b) {
+    if (!request_ok(req[b], C, H, W, nmax, true)) {
+      if (blockIdx.x == 0 && warp == 0 && lane == 0) atomicOr(status, FDL_ST_BAD_REQUEST);
+      continue;
+    }
+    const fdl_request r = req[b];
+    const df theta = theta_of(r);
+    if (shifts == nullptr && b + 1 < Bact) {
+      const fdl_request r2 = req[b + 1];
+      const int k1 = pair_class(r), k2 = pair_class(r2);
+      if (k1 >= 0 && k1 == k2 && same_fdl(r, r2) && request_ok(r2, C, H, W, nmax, true)) {
+        float2 a1[4], a2[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a1[c] = a2[c] = make_float2(0.f, 0.f);
+        const df th2 = theta_of(r2);
+        if (k1 == 0)
+          render_pair<CC, 0, false, 2>(r, r2, C, theta, th2, wabs, valid, nullptr, nullptr, lane, a1, a2, plane, off);
+        else
+          render_pair<CC, 1, false, 2>(r, r2, C, theta, th2, wabs, valid, nullptr, nullptr, lane, a1, a2, plane, off);
+        put(b, a1);
+        put(b + 1, a2);
+        ++b;
+        continue;
+      }
+    }
+    float2 acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+    const float2* shb = shifts ? reinterpret_cast<const float2*>(shifts) + (long long)b * r.N : nullptr;
+    render_terms<CC, 4>(r, 0, 1, C, theta, fq.wy, fq.wx, wabs, plane, off, valid, nullptr, nullptr, lane, acc, shb, fq);
+    put(b, acc);
   }
 }
 
@@ -432,11 +532,10 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render_grp(const fdl_requ
     };
     if (staged) {
       __syncthreads();  // the previous staged work item's reads of tile and dsh are done
-      const float2* x0 = reinterpret_cast<const float2*>(r0.layers);
-      // element e = (layer, channel) e / 32 at this thread's own frequency (e % 32 = lane)
-      for (int e = threadIdx.x; e < N * C * 32; e += blockDim.x)
-        tile[e] = valid ? __ldg(x0 + (long long)(e >> 5) * plane + off) : make_float2(0.f, 0.f);
+      stage_async(tile, reinterpret_cast<const float2*>(r0.layers), N * C, plane, off, valid);
+      cp_async_commit();
       for (int k = threadIdx.x; k < N; k += blockDim.x) dsh[k] = __ldg(r0.d + k);
+      cp_async_wait<0>();
       __syncthreads();
     } else if (q - lane >= Qs) {
       continue;  // this warp's 32 frequencies lie past the image
@@ -483,9 +582,6 @@ __global__ void __launch_bounds__(kRenderWarps * 32) k_render_grp(const fdl_requ
   }
 }
 
-__device__ __forceinline__ bool same_fdl(const fdl_request& a, const fdl_request& b) {
-  return a.layers == b.layers && a.d == b.d && a.N == b.N && a.H == b.H && a.W == b.W && a.C == b.C;
-}
 
 // *gate = 1 when every active request passes request_ok with exactly (C, H, W) and reads the
 // same FDL (layers, d, N) as request 0 (the tiled path), else 0.  plan = [ngroups, tiles,
@@ -820,14 +916,20 @@ cudaError_t launch_render_spectra(const fdl_request* req, int B, const int* coun
   const int Qs = H * (W / 2 + 1);
   const int tile_lc = min(Nmax * C, kTileMaxLC);
   const size_t smem = (size_t)tile_lc * 32 * sizeof(float2);
+  const int ntiles = (Qs + 31) / 32;
   cudaError_t e = cudaSuccess;
-  // the channel loop unrolled for one and three channels, predicated up to four otherwise
+  // the channel loop unrolled for one and three channels, predicated up to four otherwise;
+  // fewer than 8 requests: k_render_few, a warp per 32 bins
 #define FDL_RENDER(CC)                                                                                         \
-  {                                                                                                            \
+  if (B < kRenderWarps) {                                                                                      \
+    k_render_few<CC><<<(ntiles + kFewWarps - 1) / kFewWarps, kFewWarps * 32, 0, st>>>(req, B, count, C, H, W,  \
+                                                                                      Nmax, out, shifts,       \
+                                                                                      status, gate);           \
+  } else {                                                                                                     \
     e = set_smem((const void*)k_render<CC>, (size_t)kTileMaxLC * 32 * sizeof(float2));                        \
     if (e != cudaSuccess) return e;                                                                            \
-    k_render<CC><<<(Qs + 31) / 32, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, Nmax, out,  \
-                                                                  shifts, status, gate);                       \
+    k_render<CC><<<ntiles, kRenderWarps * 32, smem, st>>>(req, B, count, C, H, W, tile_lc, Nmax, out, shifts,  \
+                                                          status, gate);                                       \
   }
   if (C == 1) FDL_RENDER(1)
   else if (C == 3) FDL_RENDER(3)
