@@ -87,6 +87,34 @@ def test_mixed_fdls_in_one_call_and_batch_count(fdl):
     assert torch.all(specs[3].out == -7.0)  # beyond the count: untouched
 
 
+def test_device_count_below_eight_on_one_fdl(fdl):
+    """A launch for 8 requests of one FDL with 1, 2, 5 and 7 of them active (a device count, as
+    in a captured serving batch): the tiled render stages the layer values for the active
+    requests and leaves the rest untouched; pairs of views, of discs and lone squares."""
+    X = random_layer_spectra(6, 10, 3, 32, 64)
+    d = np.linspace(-2.5, 2, 10).astype(np.float32)
+    Xd, dd = _dev(X), _dev(d)
+    rng = np.random.default_rng(3)
+    kinds = ["pinhole", "pinhole", "disc", "disc", "square", "pinhole", "disc", "square"]
+    specs = [fdl.RenderSpec(Xd, dd, tuple(rng.uniform(-3, 3, 2)), float(rng.uniform(-2, 2)), k,
+                            0.0 if k == "pinhole" else float(rng.uniform(0.3, 2.0))) for k in kinds]
+    ap = {"pinhole": O.AP_PINHOLE, "disc": O.AP_DISC, "square": O.AP_SQUARE}
+    refs = [O.render(X.astype(np.complex128), d.astype(np.float64), sp.u0, sp.s, ap[sp.aperture], sp.radius)
+            for sp in specs]
+    for n in (1, 2, 5, 7):
+        for sp in specs:
+            sp.out = torch.full((3, 32, 64), -7.0, device="cuda")
+        req = fdl.pack_requests(specs, "cuda")
+        count = torch.tensor([n], dtype=torch.int32, device="cuda")
+        ws = fdl.refocus(req, 8, 3, 32, 64, 10, count=count)
+        assert fdl.sync_status(ws) == 0
+        for i, sp in enumerate(specs):
+            if i < n:
+                assert np.max(np.abs(sp.out.cpu().numpy() - refs[i])) < TOL
+            else:
+                assert torch.all(sp.out == -7.0)
+
+
 def test_full_size_render(fdl):
     """512x512 RGB, 30 layers (the rendering side of the 9x9 workload), four views + four refocus."""
     X = random_layer_spectra(4, 30, 3, 512, 512)
