@@ -265,13 +265,14 @@ __device__ __forceinline__ int pair_class(const fdl_request& r) {
   return r.aperture == FDL_AP_DISC ? 1 : -1;
 }
 
-// CTA: 32 consecutive stored bins (lane = bin) x 8 warps.
-//  * B >= 8 requests: warp w renders requests w, w + 8, ...; when every request reads
-//    the same FDL (and N*C <= tile_lc) the CTA first stages that FDL's layer values for
+// CTA: 32 consecutive stored bins (lane = bin) x 8 warps; launched for B >= 8 requests
+// (k_render_few takes smaller launches).
+//  * 8 or more active requests: warp w renders requests w, w + 8, ...; when every request
+//    reads the same FDL (and N*C <= tile_lc) the CTA first stages that FDL's layer values for
 //    its 32 bins in shared memory and all requests read them there.
-//  * B < 8 (single renders, small batches): the 8 / B warps given to a request split its
-//    layers and their partial sums are added through shared memory, so that one request
-//    still occupies the whole CTA.
+//  * fewer than 8 active (a device-side count below B, as in a captured serving batch): the
+//    8 / count warps given to a request split its layers and their partial sums are added
+//    through shared memory, so that one request still occupies the whole CTA.
 template <int CC>
 __global__ void __launch_bounds__(kRenderWarps * 32) k_render(const fdl_request* __restrict__ req, int B,
                                                               const int* __restrict__ count, int C, int H, int W,
