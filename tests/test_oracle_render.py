@@ -189,3 +189,22 @@ def test_render_with_a_one_pixel_table_is_the_pinhole_render():
     a = O.render(X, d, (0.3, -0.2), 0.7, O.AP_TABLE, 0.4, T)
     b = O.render(X, d, (0.3, -0.2), 0.7, O.AP_PINHOLE, 0.0)
     assert np.allclose(a, b, atol=1e-13)
+
+
+@pytest.mark.parametrize("H,W", [(15, 21), (16, 24)])
+@pytest.mark.parametrize("kind,radius", [(O.AP_PINHOLE, 0.0), (O.AP_DISC, 1.3), (O.AP_SQUARE, 0.8),
+                                         (O.AP_POINTS, 0.0)])
+def test_rendered_spectrum_of_real_layers_is_hermitian(H, W, kind, radius):
+    """Real layers and a real aperture give a real image, so the stored kx = 0 column of the
+    rendered spectrum obeys B(-w_y, 0) = conj B(w_y, 0) (Sec. VII) for any non-integer u0, s and
+    d_k; the even-H Nyquist row, whose partner is itself, is left out.  A frequency mapped
+    without its sign (k / H instead of (k - H) / H past the middle) breaks it."""
+    _, X = _layers(11, 5, 2, H, W)
+    d = np.array([-2.3, -0.7, 0.4, 1.1, 2.6])
+    pts = np.array([[0.0, 0.0], [1.3, -0.4], [-0.6, 2.1]])  # not symmetric: psi_hat is complex
+    B = O.render_spectrum(X, d, (0.37, -1.41), 0.55, kind, radius, pts if kind == O.AP_POINTS else None, W)
+    rows = [ky for ky in range(1, H) if 2 * ky != H]
+    mirror = [(H - ky) % H for ky in rows]
+    scale = np.abs(B[:, :, 0]).max()
+    assert np.max(np.abs(B[:, mirror, 0] - np.conj(B[:, rows, 0]))) < 1e-12 * scale
+    assert np.max(np.abs(B[:, 0, 0].imag)) < 1e-12 * scale  # the DC bin is real
